@@ -1,0 +1,324 @@
+"""Pins of the oracle's time loop against closed forms, exact discrete
+balances, textbook special cases and invariants.
+
+Every case is seeded and small enough to run in seconds on one CPU core.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import media
+
+E = np.array([(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1),
+              (1, 1), (-1, 1), (-1, -1), (1, -1)], dtype=int)
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+MAGIC_TAU = 0.5 + math.sqrt(3.0) / 4.0  # (tau - 1/2)^2 = 3/16
+
+
+def run(orc, eps, K, g, tau=1.0, periodic_y=False, steps=20000, tol=1e-14,
+        check=100, feps=0.0, literal=False):
+    ny, nx = eps.shape
+    o = orc.Oracle(nx, ny, tau=tau, periodic_y=periodic_y, literal=literal)
+    o.set_medium(eps, K, feps)
+    o.set_force(*g)
+    o.step(steps, tol=tol, check_every=check)
+    return o
+
+
+# -- exact fixed points --------------------------------------------------
+
+@pytest.mark.parametrize("eps,K,tau,G", [
+    (0.5, 1e-2, 1.0, 1e-5), (0.1, 1e-4, 0.8, 1e-6),
+    (1.0, 3.0, 1.7, 1e-6), (0.25, 5e-3, 0.55, 2e-6)])
+def test_uniform_darcy_fixed_point(orc, eps, K, tau, G):
+    """Uniform medium, periodic x and y, F_eps = 0: the steady state must be
+    the Darcy velocity u = K G / nu (uniform state needs f - f_eq = tau F_i;
+    its first moment forces F = 0, i.e. eps nu u / K = eps G).  The oracle
+    stores absolute f ~ 0.1-0.4 in FP64, so u is resolved to a few ulps of
+    f: an absolute floor of 2e-16 on top of the relative bound."""
+    e, k = media.uniform_medium(4, 4, eps, K)
+    o = run(orc, e, k, (G, 0.0), tau=tau, periodic_y=True, steps=200000,
+            tol=1e-15, check=50)
+    nu = (tau - 0.5) / 3
+    np.testing.assert_allclose(o.ux, K * G / nu, rtol=1e-9, atol=2e-16)
+    np.testing.assert_allclose(o.uy, 0.0, atol=1e-20)
+    np.testing.assert_allclose(o.rho, 1.0, rtol=1e-14)
+    assert o.permeability() == pytest.approx(K, rel=1e-9, abs=2e-16 * nu / G)
+
+
+@pytest.mark.parametrize("feps_mode,eps,K,G", [(10.0, 0.6, 1.0, 1e-3),
+                                               (-1.0, 0.4, 100.0, 5e-5)])
+def test_uniform_forchheimer_fixed_point(orc, feps_mode, eps, K, G):
+    """With the Forchheimer drag (Eq. 27), a uniform steady state satisfies
+    (nu/K) u + (F_eps/sqrt K) u^2 = G; solved in closed form."""
+    tau = 1.0
+    nu = (tau - 0.5) / 3
+    fe = feps_mode if feps_mode > 0 else 1.75 / math.sqrt(150 * eps ** 3)
+    a, b = fe / math.sqrt(K), nu / K
+    u_exact = (-b + math.sqrt(b * b + 4 * a * G)) / (2 * a)
+    assert u_exact < 0.9 * G / b  # the quadratic term really matters
+    e, k = media.uniform_medium(4, 4, eps, K)
+    o = run(orc, e, k, (G, 0.0), periodic_y=True, steps=400000, tol=1e-15,
+            check=50, feps=feps_mode)
+    np.testing.assert_allclose(o.ux, u_exact, rtol=1e-11)
+
+
+def test_poiseuille_exact_at_magic_tau(orc):
+    """Clear channel (eps = 1, K = inf) between halfway bounce-back walls:
+    standard D2Q9 BGK with Guo forcing, whose steady profile is the exact
+    parabola G/(2nu)(y+1/2)(ny-1/2-y) when (tau-1/2)^2 = 3/16.  The mean
+    gives K_app = (H^2 + 1/2)/12."""
+    ny = 16
+    e, k = media.uniform_medium(4, ny, 1.0, math.inf)
+    G = 1e-6
+    o = run(orc, e, k, (G, 0.0), tau=MAGIC_TAU, steps=400000, tol=1e-15)
+    nu = (MAGIC_TAU - 0.5) / 3
+    y = np.arange(ny)
+    prof = G / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    np.testing.assert_allclose(o.ux, np.broadcast_to(prof[:, None], (ny, 4)),
+                               rtol=1e-9)
+    assert o.permeability() == pytest.approx((ny ** 2 + 0.5) / 12, rel=1e-9)
+
+
+def test_poiseuille_slip_shrinks_at_tau_one(orc):
+    """At tau = 1 bounce-back carries a wall slip; the relative error of
+    K_app must be O(1/H^2): about 4x smaller per doubling of H."""
+    errs = []
+    for ny in (8, 16, 32):
+        e, k = media.uniform_medium(2, ny, 1.0, math.inf)
+        o = run(orc, e, k, (1e-6, 0.0), tau=1.0, steps=400000, tol=1e-14)
+        errs.append(abs(o.permeability() / ((ny ** 2 + 0.5) / 12) - 1))
+    assert errs[0] > 0
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def brinkman(s, H, eps, K, G, nu):
+    r = math.sqrt(eps / K)
+    return G * K / nu * (1 - np.cosh(r * (s - H / 2)) / np.cosh(r * H / 2))
+
+
+def test_brinkman_channel_second_order(orc):
+    """Uniform porous channel with walls: the generalized NS equation
+    (Eq. 26) reduces to nu u'' - (eps nu / K) u + eps G = 0, whose solution is
+    the cosh profile.  Refining H with K ~ H^2 (fixed Brinkman number) must
+    shrink the relative L2 error at second order."""
+    eps, tau = 0.5, 1.0
+    nu = (tau - 0.5) / 3
+    errs = []
+    for H in (16, 32, 64):
+        K = eps * (H / 8.0) ** 2
+        G = 1e-4 * nu / K
+        e, k = media.uniform_medium(2, H, eps, K)
+        o = run(orc, e, k, (G, 0.0), tau=tau, steps=400000, tol=1e-14)
+        s = np.arange(H) + 0.5
+        exact = brinkman(s, H, eps, K, G, nu)
+        num = o.ux[:, 0]
+        errs.append(np.linalg.norm(num - exact) / np.linalg.norm(exact))
+    assert errs[-1] < 5e-4
+    assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.8
+
+
+def test_series_layers_momentum_balance(orc):
+    """Layers perpendicular to the flow, periodic x and y (the paper's
+    'series' arrangements): Guo forcing adds exactly rho*F of momentum per
+    node, and periodic streaming conserves it, so the steady state has
+    sum rho F_x = 0 up to the oracle's FP64 floor (momentum resolved to
+    ~1e-16 per node, times the drag-to-c0 ratio below 2, summed over N
+    nodes).  With u nearly uniform this gives K_eff = <eps> / <eps/K>
+    (eps-weighted harmonic mean)."""
+    layers = [(8, 0.1, 1e-3), (4, 0.15, 4e-3), (12, 0.1, 2e-4), (8, 0.3, 1e-2)]
+    nx = sum(t for t, _, _ in layers)
+    eps, K = media.layered_medium(nx, 4, layers, "x")
+    G, tau = 1e-7, 1.0
+    nu = (tau - 0.5) / 3
+    o = run(orc, eps, K, (G, 0.0), tau=tau, periodic_y=True, steps=400000,
+            tol=1e-14)
+    Fx = -eps * nu / K * o.ux + eps * G
+    assert abs(np.sum(o.rho * Fx)) < 1e-15 * eps.size
+    assert 1e-15 * eps.size < 1e-6 * np.sum(o.rho * eps * G)
+    keff = eps.mean() / (eps / K).mean()
+    assert o.permeability() == pytest.approx(keff, rel=1e-4)
+
+
+def test_parallel_layers_arithmetic_mean(orc):
+    """Layers parallel to the flow, periodic y (the 'parallel' arrangement):
+    away from Brinkman layers of width sqrt(K/eps) each layer carries its
+    Darcy flux, so K_eff tends to the thickness-weighted mean of K; the
+    error shrinks as the layers thicken."""
+    errs = []
+    for t in (4, 16):
+        layers = [(t, 0.2, 1e-3), (t, 0.2, 1e-2), (2 * t, 0.15, 3e-3)]
+        ny = 4 * t
+        eps, K = media.layered_medium(4, ny, layers, "y")
+        o = run(orc, eps, K, (1e-6, 0.0), periodic_y=True, steps=400000,
+                tol=1e-14)
+        errs.append(abs(o.permeability() / K.mean() - 1))
+    assert errs[1] < errs[0]
+    assert errs[1] < 2 * math.sqrt(1e-2 / 0.2) / 16
+
+
+# -- dynamics -------------------------------------------------------------
+
+@pytest.mark.parametrize("eps", [1.0, 0.5])
+def test_taylor_green_viscosity(orc, eps):
+    """A small Taylor-Green vortex in a drag-free medium (K = inf) decays as
+    exp(-2 nu k^2 t) with nu = (tau - 1/2)/3; the porosity only enters the
+    O(u^2) momentum flux, so it must not change the decay rate."""
+    L, tau, U0 = 48, 0.8, 1e-5
+    nu = (tau - 0.5) / 3
+    k = 2 * math.pi / L
+    x = np.arange(L)
+    X, Y = np.meshgrid(x, x)
+    ux = -U0 * np.cos(k * X) * np.sin(k * Y)
+    uy = U0 * np.sin(k * X) * np.cos(k * Y)
+    e, K = media.uniform_medium(L, L, eps, math.inf)
+    o = orc.Oracle(L, L, tau=tau, periodic_y=True)
+    o.set_medium(e, K)
+    o.set_force(0.0, 0.0)
+    o.init_equilibrium(None, ux, uy)
+    mode = -np.cos(k * X) * np.sin(k * Y)
+
+    def amp():
+        return np.sum(o.ux * mode) / np.sum(mode * mode)
+
+    o.step(50)
+    a1 = amp()
+    o.step(300)
+    a2 = amp()
+    rate = -math.log(a2 / a1) / 300
+    assert rate == pytest.approx(2 * nu * k * k, rel=5e-3)
+
+
+def test_mass_conservation(orc):
+    """Streaming and bounce-back move populations, collision conserves
+    sum f (sum F_i = 0), so total mass is constant every step up to FP64
+    round-off, on a random heterogeneous medium with walls."""
+    eps, K = media.random_medium(24, 20, seed=3)
+    o = orc.Oracle(24, 20, tau=0.7)
+    o.set_medium(eps, K, -1.0)
+    o.set_force(3e-4, -1e-4)
+    m0 = o.f.sum()
+    masses = []
+    for _ in range(10):
+        o.step(50)
+        masses.append(o.f.sum())
+    assert np.max(np.abs(np.array(masses) / m0 - 1)) < 1e-13
+
+
+def textbook_bgk_guo(f, tau, G, steps, walls=True):
+    """Standard D2Q9 BGK with Guo forcing (body force G per unit mass),
+    streaming by np.roll, halfway bounce-back walls in y: the eps = 1,
+    K = inf special case of the GLBM, written in its textbook form."""
+    f = f.copy()
+    for _ in range(steps):
+        post = f
+        g = np.empty_like(post)
+        for i in range(9):
+            g[i] = np.roll(np.roll(post[i], E[i, 0], axis=1), E[i, 1], axis=0)
+        if walls:
+            for i in range(9):
+                if E[i, 1] == 1:
+                    g[i][0, :] = post[OPP[i]][0, :]
+                if E[i, 1] == -1:
+                    g[i][-1, :] = post[OPP[i]][-1, :]
+        rho = g.sum(0)
+        ux = (np.tensordot(E[:, 0], g, 1) + 0.5 * rho * G[0]) / rho
+        uy = (np.tensordot(E[:, 1], g, 1) + 0.5 * rho * G[1]) / rho
+        out = np.empty_like(g)
+        for i in range(9):
+            cu = E[i, 0] * ux + E[i, 1] * uy
+            feq = W[i] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+            # Guo: (1 - 1/2tau) w_i [ (e_i - u)/cs^2 + (e_i.u) e_i / cs^4 ] . rho G
+            fx = 3 * (E[i, 0] - ux) + 9 * cu * E[i, 0]
+            fy = 3 * (E[i, 1] - uy) + 9 * cu * E[i, 1]
+            Fi = (1 - 0.5 / tau) * W[i] * rho * (fx * G[0] + fy * G[1])
+            out[i] = g[i] - (g[i] - feq) / tau + Fi
+        f = out
+    return f, ux, uy
+
+
+@pytest.mark.parametrize("walls", [True, False])
+def test_reduces_to_textbook_bgk_guo(orc, walls):
+    """eps = 1 and K = inf turn the GLBM into plain BGK + Guo forcing; a
+    random warm state advanced 25 steps must agree with a textbook
+    implementation (different streaming and boundary mechanics)."""
+    nx, ny = 7, 6
+    rho, ux, uy = media.random_state(nx, ny, seed=11, amp=1e-2, u_amp=0.03)
+    e, k = media.uniform_medium(nx, ny, 1.0, math.inf)
+    G = (2e-4, -1e-4)
+    o = orc.Oracle(nx, ny, tau=0.85, periodic_y=not walls)
+    o.set_medium(e, k)
+    o.set_force(*G)
+    o.init_equilibrium(rho, ux, uy)
+    f0 = o.f.copy()
+    o.step(25)
+    ft, uxt, uyt = textbook_bgk_guo(f0, 0.85, G, 25, walls=walls)
+    np.testing.assert_allclose(o.f, ft, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(o.ux, uxt, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(o.uy, uyt, rtol=0, atol=1e-15)
+
+
+def test_mirror_symmetry_with_walls(orc):
+    """A medium symmetric under y -> ny-1-y, with walls and a force along x,
+    gives u_x symmetric and u_y antisymmetric (bottom and top walls are
+    handled consistently)."""
+    eps, K = media.random_medium(10, 12, seed=5)
+    eps = np.concatenate([eps[:6], eps[:6][::-1]])
+    K = np.concatenate([K[:6], K[:6][::-1]])
+    o = run(orc, eps, K, (1e-4, 0.0), tau=0.9, steps=300, tol=0)
+    scale = np.abs(o.ux).max()
+    np.testing.assert_allclose(o.ux, o.ux[::-1], atol=1e-12 * scale)
+    np.testing.assert_allclose(o.uy, -o.uy[::-1], atol=1e-12 * scale)
+
+
+def test_velocity_linear_in_force(orc):
+    """The Darcy regime is linear: doubling G doubles u up to relative O(u)."""
+    eps, K, _ = media.two_phase_medium(32, 32, seed=2)
+    a = run(orc, eps, K, (1e-6, 0.0), steps=400, tol=0)
+    b = run(orc, eps, K, (2e-6, 0.0), steps=400, tol=0)
+    umax = np.abs(b.ux).max()
+    np.testing.assert_allclose(b.ux, 2 * a.ux, rtol=0, atol=100 * umax * umax + 1e-9 * umax)
+
+
+# -- reduction, schedule, builds ------------------------------------------
+
+def test_mean_velocity_matches_fsum(orc):
+    """A8/A9: the mean velocity equals the exactly rounded mean of the
+    exported field (math.fsum) to FP64 precision."""
+    eps, K, _ = media.two_phase_medium(40, 24, seed=7)
+    o = run(orc, eps, K, (1e-6, 0.0), steps=250, tol=0)
+    N = eps.size
+    assert o.mean_u[0] == pytest.approx(math.fsum(o.ux.ravel()) / N, rel=1e-13)
+    assert o.mean_u[1] == pytest.approx(math.fsum(o.uy.ravel()) / N,
+                                        abs=1e-13 * abs(o.mean_u[0]))
+
+
+def test_convergence_schedule_and_resume(orc):
+    """Chunks of check_every steps; the test compares the mean u_x with the
+    previous check, across calls.  Split calls reproduce one call bitwise."""
+    eps, K, _ = media.two_phase_medium(16, 16, seed=1)
+    a = orc.Oracle(16, 16)
+    a.set_medium(eps, K)
+    a.set_force(1e-6)
+    done, conv = a.step(100000, tol=1e-9, check_every=50)
+    assert conv and done % 50 == 0 and 100 < done < 100000
+    b = orc.Oracle(16, 16)
+    b.set_medium(eps, K)
+    b.set_force(1e-6)
+    d1, c1 = b.step(100, tol=1e-9, check_every=50)
+    d2, c2 = b.step(100000, tol=1e-9, check_every=50)
+    assert not c1 and c2 and d1 + d2 == done
+    assert np.array_equal(a.f, b.f)
+
+
+def test_openmp_build_bitwise(orc):
+    eps, K, _ = media.two_phase_medium(64, 32, seed=4)
+    a = run(orc, eps, K, (1e-6, 0.0), steps=30, tol=0)
+    o = orc.Oracle(64, 32, threads=4)
+    o.set_medium(eps, K)
+    o.set_force(1e-6)
+    o.step(30)
+    assert np.array_equal(a.f, o.f) and np.array_equal(a.mean_u, o.mean_u)
