@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""GLBM throughput benchmark: lattice node updates per second (GLUPS) and the
+fused step kernel's fraction of the HBM roofline, on one two-phase shale
+medium per GPU.
+
+One benchmark step = one ``glbm_step`` call of ``--chunk`` time steps
+(the fused stream+collide kernel ``--chunk`` times, the last one also
+producing the FP64 mean-velocity partials, plus the reduction finalize),
+i.e. every step of the hot path; the Darcy permeability is read at the end.
+
+Default workload: 4096x4096 D2Q9 lattice, two-phase OM/IOM medium (OM
+fraction 0.2 grown with correlation length 8 nodes, eps 0.10/0.15, K
+log-uniform [1e-4,1e-3] / [5e-4,5e-3]), G = 1e-6 along x, tau = 1, walls in
+y, FP32 deviation storage.  Inputs (1.3 GB of distributions) are far larger
+than the 129 MB L2, so no flush is needed between iterations.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun): every rank advances its own medium (seed = rank);
+there is no exchange on the data path (weak scaling).  The printed value is
+the node updates of all ranks over the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GLBM GLUPS & % HBM roofline; time-to-permeability (warm/low-prec vs plain)"
+UNIT = "GLUPS"
+G = 1e-6
+TAU = 1.0
+# bytes moved per node update by the fused step kernel (algorithmic):
+# 9 populations read + 9 written, plus the packed coefficients (alpha, eps).
+ELEM = {"f32": 4, "f64": 8, "f16": 2, "bf16": 2}
+COEF = {"f32": 8, "f64": 16, "f16": 8, "bf16": 8}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def args_():
+    p = argparse.ArgumentParser(description=__doc__,
+                                formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--nx", type=int, default=4096)
+    p.add_argument("--ny", type=int, default=4096)
+    p.add_argument("--chunk", type=int, default=500,
+                   help="lattice time steps per benchmark step")
+    p.add_argument("--storage", default="f32", choices=list(ELEM))
+    p.add_argument("--om-fraction", type=float, default=0.2)
+    p.add_argument("--corr-len", type=float, default=8.0)
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="CPU-oracle sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload(a, rank=0):
+    return {
+        "workload": (f"GLBM D2Q9 {a.nx}x{a.ny} two-phase OM/IOM medium "
+                     f"(OM fraction {a.om_fraction}, correlation length "
+                     f"{a.corr_len:g}, eps 0.10/0.15, K log-uniform "
+                     f"[1e-4,1e-3]/[5e-4,5e-3], seed {a.seed + rank}), "
+                     f"G={G:g} along x, tau={TAU:g}, walls in y"),
+        "nx": a.nx, "ny": a.ny, "storage": a.storage,
+        "lb_steps_per_step": a.chunk,
+        "l2": "no flush: 1.2 GB of distributions per step >> 129 MB L2",
+    }
+
+
+def make_medium(a, rank=0):
+    import media
+    eps, K, _ = media.two_phase_medium(a.nx, a.ny, om_fraction=a.om_fraction,
+                                       corr_len=a.corr_len, seed=a.seed + rank)
+    return eps, K
+
+
+# -- distributed plumbing --------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# -- clocks ---------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and parts[1] != self.uuid:
+                    continue
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[6:10]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[4]) for r in rows
+                                    if r[4].replace(".", "").isdigit()), default=None)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        return None
+
+
+# -- roofline evidence ----------------------------------------------------
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    h.update(open(os.path.join(ROOT, "paper_1601_00704_gb300", "csrc", "glbm.cu"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(storage, nx, ny):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    scaled to this lattice; None if absent or taken from other source code."""
+    path = os.path.join(ROOT, "profiles", f"k_step_{storage}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_b = re.search(r"dram_bytes_per_node_update:\s*([0-9.eE+-]+)", text)
+    if not (m_src and m_b) or m_src.group(1) != source_hash():
+        return None
+    return float(m_b.group(1)) * nx * ny
+
+
+# -- CPU oracle timing ------------------------------------------------------
+
+def oracle_sample(a, eps, K, seconds, nsteps=None):
+    """Time the FP64 oracle (OpenMP build, all host cores) on the same
+    medium for a bounded number of time steps; returns (GLUPS, cores, steps, s)."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(a.nx, a.ny, tau=TAU, threads=os.cpu_count())
+    cores = oracle._lib(True).orc_threads(0)
+    o.set_medium(eps, K)
+    o.set_force(G)
+    if nsteps is None:
+        t0 = time.perf_counter()
+        o.step(1)
+        t1 = time.perf_counter() - t0
+        nsteps = max(1, min(500, int(seconds / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    return a.nx * a.ny * nsteps / dt / 1e9, cores, nsteps, dt
+
+
+def cpu_desc():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return model
+
+
+# -- arms ---------------------------------------------------------------------
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return 0
+    eps, K = make_medium(a)
+    # each benchmark step: a bounded sample of the same workload (full lattice,
+    # a few time steps), sized so warm-up + timed steps stay within minutes
+    per = max(5.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
+    g1, cores, n, dt = oracle_sample(a, eps, K, per)
+    times = []
+    for i in range(a.warmup + a.steps):
+        g, cores, _, dt = oracle_sample(a, eps, K, per, nsteps=n)
+        if i >= a.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = a.nx * a.ny * n * a.steps / tot / 1e9
+    cfg = workload(a)
+    cfg["lb_steps_per_step"] = n
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Gaussian-random-field two-phase medium)",
+        "config": cfg,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} time steps of the full {a.nx}x{a.ny} lattice per "
+                                   f"step, FP64 oracle, OpenMP over rows on {cpu_desc()}"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1601_00704_gb300 as pkg
+    from paper_1601_00704_gb300 import build as pbuild
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: a CUDA device is required")
+    torch.cuda.set_device(local)
+    pbuild.build()
+    eps, K = make_medium(a, rank)
+    N = a.nx * a.ny
+    stream = torch.cuda.Stream()
+    s = pkg.Solver(a.nx, a.ny, tau=TAU, storage=a.storage, walls=True, stream=stream)
+    s.set_medium(eps, K)
+    s.set_force(G, 0.0)
+    for _ in range(a.warmup):
+        s.step(a.chunk)
+    torch.cuda.synchronize()
+    barrier(world)
+    _, l0 = s.counters()
+    clocks = Clocks(gpu_uuid())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        s.step(a.chunk)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    barrier(world)
+    _, l1 = s.counters()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    kapp = s.permeability()
+    updates = N * a.chunk * a.steps
+    value = world * updates / (ms * 1e-3) / 1e9
+    # dominant kernel: the fused step, chunk launches per benchmark step
+    # (the finalize kernel adds ~3 us per chunk, included here)
+    bpu = 18 * ELEM[a.storage] + COEF[a.storage]
+    per_launch_s = ms * 1e-3 / (a.chunk * a.steps)
+    achieved = bpu * N / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(a.storage, a.nx, a.ny),
+            "peak_kind": peak_kind, "bytes_per_node_update": bpu,
+            "kernel": f"k_step<{a.storage}> (fused pull-stream + collide)",
+            "launch_us": per_launch_s * 1e6}
+
+    e2e = None
+    if not a.no_e2e:
+        # the same metric through the public API from pinned host buffers:
+        # set_medium (H2D of eps, K) + chunk steps + K_app read-back per step
+        pe = torch.from_numpy(eps).pin_memory()
+        pk = torch.from_numpy(K).pin_memory()
+        he, hk = pe.numpy(), pk.numpy()
+        for _ in range(1):
+            s.set_medium(he, hk)
+            s.step(a.chunk)
+            s.permeability()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            s.set_medium(he, hk)
+            s.step(a.chunk)
+            s.permeability()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * updates / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * N, "d2h_bytes_per_step": 40}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        g, cores, n, dt = oracle_sample(a, eps, K, a.cpu_seconds)
+        cpu = {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} time steps of the full {a.nx}x{a.ny} lattice ({dt:.1f} s), "
+                         f"FP64 oracle, OpenMP over rows on {cpu_desc()}"}
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": a.storage,
+            "data": "synthetic (seeded Gaussian-random-field two-phase medium)",
+            "config": workload(a),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": l1 - l0, "k_app": kapp,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = args_()
+    world, rank, local = dist_setup()
+    if a.impl == "reference":
+        rc = run_reference(a, world, rank)
+    else:
+        rc = run_ours(a, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

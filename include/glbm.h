@@ -1,0 +1,150 @@
+/*
+ * glbm.h - C ABI of the GB300 generalized lattice Boltzmann model (GLBM)
+ * library: gas flow through a voxelised two-phase shale matrix in which every
+ * lattice node carries its own porosity eps(x) and apparent permeability
+ * K(x), after Wang, Chen, Kang & Rahman, arXiv:1601.00704, Sec. 2.3.
+ *
+ * One time step (Eq. 29) is: pull-stream the distributions, form rho and the
+ * first moment (Eqs. 32-33), the temporal velocity v (Eq. 35), the node
+ * velocity u from the explicit quadratic solve (Eq. 34 with c0, c1 of
+ * Eqs. 36-37), the total body force F (Eq. 27; Eq. 28 when F_eps = 0), the
+ * porosity-weighted equilibrium (Eq. 30) and the forcing term (Eq. 31), then
+ * BGK-collide.  The loop repeats until the mean velocity converges; the
+ * sample's apparent permeability then follows from Darcy's law.
+ *
+ * Conventions (all entry points):
+ *  - Lattice units: dx = dt = c = 1, D2Q9, c_s^2 = 1/3, nu = (tau - 1/2)/3.
+ *  - Arrays are row-major [ny][nx] (x fastest), FP64, unless stated.
+ *  - Pointer arguments are BORROWED for the duration of the call: the caller
+ *    keeps ownership; nothing is retained.  `device_ptrs != 0` means the
+ *    arrays live in device memory of the handle's GPU, else host memory.
+ *  - The handle OWNS all device memory it allocates (distribution buffers,
+ *    packed coefficients, reduction scratch) and frees it in glbm_destroy.
+ *  - No C++ exception crosses this boundary.  Every entry point returns a
+ *    glbm_status; on failure glbm_last_error() describes it and the handle's
+ *    state is unchanged unless stated.
+ *  - A handle is not thread-safe; use one handle per host thread / stream.
+ *    Work is enqueued on the stream given to glbm_create.
+ */
+#ifndef GLBM_H
+#define GLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glbm *glbm_t;
+
+typedef enum {
+    GLBM_OK = 0,
+    GLBM_EINVAL = -1, /* bad argument (size, range, NaN, missing force) */
+    GLBM_ENOMEM = -2, /* device or pinned allocation failed */
+    GLBM_ECUDA = -3,  /* a CUDA runtime call or kernel launch failed */
+    GLBM_ENAN = -4,   /* a non-finite mean velocity was detected */
+    GLBM_ESTATE = -5  /* call not valid in the current state */
+} glbm_status;
+
+/* Storage precision of the distributions.  Collision arithmetic runs in
+ * FP32 for the 32/16-bit formats and FP64 for GLBM_F64; the convergence
+ * reduction always accumulates in FP64.  All formats store deviations
+ * g_i = f_i - w_i * rho0 (rho0 = 1) rather than f_i. */
+typedef enum {
+    GLBM_F32 = 0,
+    GLBM_F64 = 1,
+    GLBM_F16DEV = 2,  /* FP16 deviations times a power-of-two scale */
+    GLBM_BF16DEV = 3  /* BF16 deviations times a power-of-two scale */
+} glbm_storage;
+
+/* Boundary flags (the paper states none; see glbm_create). */
+#define GLBM_WALLS_Y 0u    /* halfway bounce-back walls at y=-1/2, ny-1/2 */
+#define GLBM_PERIODIC_Y 1u /* periodic in y */
+
+/*
+ * Create a solver for an nx-by-ny lattice (x is always periodic).
+ *   tau      BGK relaxation time (Eq. 29), must be > 1/2.
+ *   storage  distribution storage format (above).
+ *   flags    GLBM_WALLS_Y (default) or GLBM_PERIODIC_Y.
+ *   stream   cudaStream_t to enqueue on; NULL = the legacy default stream.
+ *   out      receives the handle.
+ * Allocates both distribution buffers, the coefficient planes and the
+ * reduction scratch on the current CUDA device.  nx, ny >= 2 and
+ * nx*ny < 2^31.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage,
+                        unsigned flags, void *stream, glbm_t *out);
+
+/*
+ * Load the medium: per-node porosity eps in (0, 1] and apparent permeability
+ * K > 0 (+inf = clear fluid), each [ny][nx] FP64.  F_eps selects the
+ * Forchheimer geometric function of Eq. 27, which the paper leaves unset:
+ * 0 = none (the paper's Eq. 28), > 0 = that constant, < 0 = Ergun's
+ * 1.75/sqrt(150 eps^3) per node.  Packs the per-node coefficients
+ * (eps*nu/K, eps and, with F_eps != 0, eps*F_eps/sqrt(K); Eqs. 36-37) on the
+ * device, resets the distributions to f_eq(rho = 1, u = 0), the step count to
+ * zero and the convergence history.  Invalid values: EINVAL, state unchanged.
+ */
+glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K,
+                            double F_eps, int device_ptrs);
+
+/* External body force G (per unit mass, lattice units) of Eq. 27.  Keeps the
+ * distributions; clears the convergence history. */
+glbm_status glbm_set_force(glbm_t h, double gx, double gy);
+
+/*
+ * Warm start: set the distributions to the porosity equilibrium of Eq. 30,
+ * f_i = f_eq_i(rho, u; eps), per node.  rho may be NULL (rho = 1); ux and uy
+ * must both be given or both NULL (u = 0).  Resets the step count and the
+ * convergence history.  Requires a medium (ESTATE otherwise).
+ */
+glbm_status glbm_init_equilibrium(glbm_t h, const double *rho,
+                                  const double *ux, const double *uy,
+                                  int device_ptrs);
+
+/*
+ * Advance at most n steps.  The steps run in chunks of check_every; the mean
+ * velocity U (FP64 over all nodes, the Eq. 34 velocities of that step) is
+ * formed at the end of every chunk when tol > 0, and at the end of the call
+ * in any case.  With tol > 0 the call stops once
+ * |Ux - Ux_prev| <= tol * |Ux| (Ux_prev = the previous such value, kept
+ * between calls) and reads a 32-byte status back after each chunk; with
+ * tol <= 0 it runs exactly n steps and returns without waiting for the GPU.
+ *   steps_done, converged  (out, may be NULL)
+ * Errors: ESTATE (no medium), EINVAL (n < 0, check_every < 1), ENAN (the
+ * state is kept for inspection), ECUDA.
+ */
+glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every,
+                      long long *steps_done, int *converged);
+
+/* Mean velocity (Ux, Uy) of the last completed step; waits for the stream.
+ * ESTATE before the first step, ENAN if it is not finite. */
+glbm_status glbm_mean_velocity(glbm_t h, double out[2]);
+
+/* Darcy apparent permeability of the sample, K_app = nu * Ux / Gx in lattice
+ * units (multiply by dx^2 for physical units).  EINVAL if Gx = 0. */
+glbm_status glbm_permeability(glbm_t h, double *kxx);
+
+/* The Eq. 34 velocity field of the last completed step, [ny][nx] FP64 each
+ * (recomputed from the pre-step state with the step's own arithmetic). */
+glbm_status glbm_get_velocity(glbm_t h, double *ux, double *uy,
+                              int device_ptrs);
+
+/* The current post-collision distributions as absolute f_i in FP64,
+ * laid out [9][ny][nx] with the D2Q9 order e0=(0,0), e1..e4=(1,0),(0,1),
+ * (-1,0),(0,-1), e5..e8=(1,1),(-1,1),(-1,-1),(1,-1). */
+glbm_status glbm_get_distributions(glbm_t h, double *f, int device_ptrs);
+
+/* Steps since the last reset, and the number of kernels this handle has
+ * launched in total (either pointer may be NULL). */
+glbm_status glbm_counters(glbm_t h, long long *steps, long long *launches);
+
+/* Release all device memory of the handle.  NULL-safe. */
+void glbm_destroy(glbm_t h);
+
+/* Message of the last failure on this handle (h = NULL: the last failure of
+ * glbm_create on this host thread).  Never NULL. */
+const char *glbm_last_error(glbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GLBM_H */

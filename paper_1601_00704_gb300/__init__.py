@@ -1,0 +1,235 @@
+"""GB300-native generalized lattice Boltzmann model (GLBM) for gas flow in
+voxelised organic shale (Wang, Chen, Kang & Rahman, arXiv:1601.00704, Sec. 2.3).
+
+Every lattice node carries its own porosity eps and apparent permeability K;
+the time loop (Eqs. 27-37) runs as hand-written CUDA kernels for sm_103a in
+``libglbm.so`` behind the C ABI of ``include/glbm.h``.  This package is the
+thin Python binding over that ABI: it marshals arguments (NumPy host arrays
+or CUDA torch tensors) and raises on error codes.  There is no CPU or
+PyTorch fallback: importing works anywhere, but creating a ``Solver`` needs
+the built library and a CUDA device, and fails loudly otherwise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB as LIB_PATH
+
+__all__ = ["Solver", "GLBMError", "load", "F32", "F64", "F16DEV", "BF16DEV",
+           "WALLS_Y", "PERIODIC_Y", "STORAGE"]
+
+F32, F64, F16DEV, BF16DEV = 0, 1, 2, 3
+STORAGE = {"f32": F32, "f64": F64, "f16": F16DEV, "bf16": BF16DEV}
+WALLS_Y, PERIODIC_Y = 0, 1
+
+_STATUS = {0: "GLBM_OK", -1: "GLBM_EINVAL", -2: "GLBM_ENOMEM",
+           -3: "GLBM_ECUDA", -4: "GLBM_ENAN", -5: "GLBM_ESTATE"}
+
+# Symbols the header declares (checked by the CPU test-suite).
+SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
+           "glbm_init_equilibrium", "glbm_step", "glbm_mean_velocity",
+           "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
+           "glbm_counters", "glbm_destroy", "glbm_last_error"]
+
+
+class GLBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = _STATUS.get(code, str(code))
+
+
+_lib = None
+_PD = C.POINTER(C.c_double)
+_VP = C.c_void_p
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libglbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libglbm.so not built at {p}; run "
+                          "paper_1601_00704_gb300.build.build() first")
+    lib = C.CDLL(p)
+    i, ll, d, h = C.c_int, C.c_longlong, C.c_double, _VP
+    sig = {
+        "glbm_create": ([i, i, d, i, C.c_uint, _VP, C.POINTER(_VP)], i),
+        "glbm_set_medium": ([h, _VP, _VP, d, i], i),
+        "glbm_set_force": ([h, d, d], i),
+        "glbm_init_equilibrium": ([h, _VP, _VP, _VP, i], i),
+        "glbm_step": ([h, ll, d, i, C.POINTER(ll), C.POINTER(i)], i),
+        "glbm_mean_velocity": ([h, _PD], i),
+        "glbm_permeability": ([h, _PD], i),
+        "glbm_get_velocity": ([h, _VP, _VP, i], i),
+        "glbm_get_distributions": ([h, _VP, i], i),
+        "glbm_counters": ([h, C.POINTER(ll), C.POINTER(ll)], i),
+        "glbm_destroy": ([h], None),
+        "glbm_last_error": ([h], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _is_tensor(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+class _Arg:
+    """Marshal one FP64 [ny][nx] (or [9][ny][nx]) array: NumPy on the host or
+    a contiguous CUDA torch tensor on the device."""
+
+    def __init__(self, a, shape, writable=False):
+        self.obj = None
+        self.device = False
+        if a is None:
+            self.ptr = None
+            return
+        if _is_tensor(a):
+            import torch
+            if a.dtype != torch.float64 or tuple(a.shape) != shape:
+                raise ValueError(f"expected float64 tensor of shape {shape}")
+            if not a.is_cuda:
+                a = a.numpy()
+            else:
+                if not a.is_contiguous():
+                    if writable:
+                        raise ValueError("output tensor must be contiguous")
+                    a = a.contiguous()
+                self.obj, self.ptr, self.device = a, a.data_ptr(), True
+                return
+        if writable:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64
+                    and a.shape == shape and a.flags.c_contiguous):
+                raise ValueError(f"output must be a C-contiguous float64 array {shape}")
+            arr = a
+        else:
+            arr = np.ascontiguousarray(a, dtype=np.float64)
+            if arr.shape != shape:
+                raise ValueError(f"expected shape {shape}, got {arr.shape}")
+        self.obj, self.ptr = arr, arr.ctypes.data
+
+
+class Solver:
+    """One GLBM lattice on the current CUDA device (a ``glbm_t`` handle).
+
+    ``storage`` is 'f32' (default), 'f64', 'f16' or 'bf16'; ``walls`` puts
+    halfway bounce-back walls at y = -1/2 and ny - 1/2 (else periodic y);
+    ``stream`` is a ``torch.cuda.Stream`` (or raw cudaStream_t int), default
+    the legacy default stream.
+    """
+
+    def __init__(self, nx, ny, tau=1.0, storage="f32", walls=True, stream=None):
+        self._lib = load()
+        self._h = _VP()
+        self.nx, self.ny, self.tau = int(nx), int(ny), float(tau)
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        s = stream
+        if s is not None and not isinstance(s, int):
+            s = s.cuda_stream
+        self._stream = s
+        rc = self._lib.glbm_create(self.nx, self.ny, self.tau, st,
+                                   WALLS_Y if walls else PERIODIC_Y,
+                                   _VP(s) if s else None, C.byref(self._h))
+        if rc != 0:
+            raise GLBMError(rc, self._lib.glbm_last_error(None).decode())
+        self.storage = storage
+        self.gx = self.gy = 0.0
+
+    # -- plumbing ----------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise GLBMError(rc, self._lib.glbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.glbm_destroy(self._h)
+            self._h = _VP()
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    @property
+    def nu(self):
+        return (self.tau - 0.5) / 3.0
+
+    # -- API ---------------------------------------------------------------
+    def set_medium(self, eps, K, F_eps=0.0):
+        e = _Arg(eps, self.shape)
+        k = _Arg(K, self.shape)
+        if e.device != k.device:
+            raise ValueError("eps and K must both be host or both device arrays")
+        self._check(self._lib.glbm_set_medium(self._h, e.ptr, k.ptr,
+                                              float(F_eps), int(e.device)))
+
+    def set_force(self, gx, gy=0.0):
+        self._check(self._lib.glbm_set_force(self._h, float(gx), float(gy)))
+        self.gx, self.gy = float(gx), float(gy)
+
+    def init_equilibrium(self, rho=None, ux=None, uy=None):
+        args = [_Arg(a, self.shape) for a in (rho, ux, uy)]
+        dev = {a.device for a in args if a.ptr is not None}
+        if len(dev) > 1:
+            raise ValueError("mixing host and device arrays")
+        self._check(self._lib.glbm_init_equilibrium(
+            self._h, args[0].ptr, args[1].ptr, args[2].ptr, int(dev == {True})))
+
+    def step(self, n, tol=0.0, check_every=100):
+        done, conv = C.c_longlong(), C.c_int()
+        self._check(self._lib.glbm_step(self._h, int(n), float(tol),
+                                        int(check_every), C.byref(done),
+                                        C.byref(conv)))
+        return done.value, bool(conv.value)
+
+    def mean_velocity(self):
+        out = (C.c_double * 2)()
+        self._check(self._lib.glbm_mean_velocity(self._h, out))
+        return np.array([out[0], out[1]])
+
+    def permeability(self):
+        k = C.c_double()
+        self._check(self._lib.glbm_permeability(self._h, C.byref(k)))
+        return k.value
+
+    def velocity(self, ux=None, uy=None):
+        """Eq. 34 velocity field of the last step -> (ux, uy); pass CUDA
+        float64 tensors to keep the result on the device."""
+        if ux is None:
+            ux, uy = np.empty(self.shape), np.empty(self.shape)
+        a, b = _Arg(ux, self.shape, True), _Arg(uy, self.shape, True)
+        self._check(self._lib.glbm_get_velocity(self._h, a.ptr, b.ptr, int(a.device)))
+        return ux, uy
+
+    def distributions(self, out=None):
+        """Absolute f_i in FP64, shape (9, ny, nx)."""
+        shp = (9,) + self.shape
+        if out is None:
+            out = np.empty(shp)
+        a = _Arg(out, shp, True)
+        self._check(self._lib.glbm_get_distributions(self._h, a.ptr, int(a.device)))
+        return out
+
+    def counters(self):
+        s, l = C.c_longlong(), C.c_longlong()
+        self._check(self._lib.glbm_counters(self._h, C.byref(s), C.byref(l)))
+        return s.value, l.value
