@@ -207,6 +207,8 @@ __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
 
 // ---------------------------------------------------------------------------
 // Pull-streaming gather of VEC consecutive nodes (x0..x0+VEC-1, row y).
+// Phase 1 issues every load of the thread (9 vectors + up to 6 edge scalars)
+// before phase 2 consumes any, so all of them are in flight together.
 // ---------------------------------------------------------------------------
 template <typename T, int VEC, bool WALLS>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo, int x0, int y,
@@ -214,58 +216,79 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
                                        typename Store<T>::R (&g)[VEC][9]) {
     using R = typename Store<T>::R;
     const int nx = geo.nx, ny = geo.ny;
+    if constexpr (VEC == 1) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const int ex = cx(i), ey = cy(i);
-        int ys = y - ey;
-        bool bb = false;
-        if (ys < 0 || ys >= ny) {
-            if (WALLS) bb = true;
-            else ys = ys < 0 ? ys + ny : ys - ny;
-        }
-        if (bb) {
-            // halfway bounce-back: the opposite population that left this
-            // node towards the wall returns reversed (same node, no shift)
-            const T *p = src + (long long)opp(i) * geo.plane + (long long)y * nx + x0;
-            if constexpr (VEC == 1) {
-                g[0][i] = active ? Store<T>::ld(p[0], inv_s) : R(0);
-            } else {
-                T v[VEC];
-                if (active) ld16<T, VEC>(p, v);
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) g[k][i] = active ? Store<T>::ld(v[k], inv_s) : R(0);
+        for (int i = 0; i < 9; ++i) {
+            int ys = y - cy(i);
+            const T *p;
+            if (ys < 0 || ys >= ny) {
+                if (WALLS) {
+                    // halfway bounce-back: the opposite population that left
+                    // this node towards the wall returns reversed
+                    p = src + (long long)opp(i) * geo.plane + (long long)y * nx + x0;
+                    g[0][i] = active ? Store<T>::ld(*p, inv_s) : R(0);
+                    continue;
+                }
+                ys = ys < 0 ? ys + ny : ys - ny;
             }
-            continue;
-        }
-        const T *row = src + (long long)i * geo.plane + (long long)ys * nx;
-        if constexpr (VEC == 1) {
-            int xs = x0 - ex;
+            int xs = x0 - cx(i);
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-            g[0][i] = active ? Store<T>::ld(row[xs], inv_s) : R(0);
-        } else {
-            R r[VEC];
-            {
-                T v[VEC];
-                if (active) ld16<T, VEC>(row + x0, v);
+            p = src + (long long)i * geo.plane + (long long)ys * nx + xs;
+            g[0][i] = active ? Store<T>::ld(*p, inv_s) : R(0);
+        }
+    } else {
+        // shift mode per population: 0 none, +1 take x-1, -1 take x+1;
+        // bounce-back rows take the same node's opposite population unshifted
+        T v[9][VEC];
+        T edge[9];
+        int mode[9];
+        const bool first = lane == 0 || x0 == 0;
+        const bool last = lane == 31 || x0 + VEC >= nx;
+        const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+        const int xr = x0 + VEC >= nx ? 0 : x0 + VEC;
 #pragma unroll
-                for (int k = 0; k < VEC; ++k) r[k] = active ? Store<T>::ld(v[k], inv_s) : R(0);
+        for (int i = 0; i < 9; ++i) {
+            int ys = y - cy(i);
+            int pl = i;
+            mode[i] = cx(i);
+            if (ys < 0 || ys >= ny) {
+                if (WALLS) {
+                    pl = opp(i);
+                    ys = y;
+                    mode[i] = 0;
+                } else {
+                    ys = ys < 0 ? ys + ny : ys - ny;
+                }
             }
-            if (ex == 0) {
+            const T *row = src + (long long)pl * geo.plane + (long long)ys * nx;
+            if (active) ld16<T, VEC>(row + x0, v[i]);
+            else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) v[i][k] = T(0);
+            }
+            edge[i] = T(0);
+            if (mode[i] == 1 && active && first) edge[i] = row[xl];
+            if (mode[i] == -1 && active && last) edge[i] = row[xr];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            R r[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) r[k] = Store<T>::ld(v[i][k], inv_s);
+            if (mode[i] == 0) {
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) g[k][i] = r[k];
-            } else if (ex == 1) {
+            } else if (mode[i] == 1) {
                 // node x takes x-1: shift right by one, left neighbour from lane-1
                 R left = __shfl_up_sync(0xffffffffu, r[VEC - 1], 1);
-                if (active && (lane == 0 || x0 == 0))
-                    left = Store<T>::ld(row[x0 == 0 ? nx - 1 : x0 - 1], inv_s);
+                if (first) left = Store<T>::ld(edge[i], inv_s);
                 g[0][i] = left;
 #pragma unroll
                 for (int k = 1; k < VEC; ++k) g[k][i] = r[k - 1];
             } else {
                 // node x takes x+1: shift left by one, right neighbour from lane+1
                 R right = __shfl_down_sync(0xffffffffu, r[0], 1);
-                if (active && (lane == 31 || x0 + VEC >= nx))
-                    right = Store<T>::ld(row[x0 + VEC >= nx ? 0 : x0 + VEC], inv_s);
+                if (last) right = Store<T>::ld(edge[i], inv_s);
 #pragma unroll
                 for (int k = 0; k < VEC - 1; ++k) g[k][i] = r[k + 1];
                 g[VEC - 1][i] = right;
