@@ -137,11 +137,59 @@ glbm_status glbm_get_distributions(glbm_t h, double *f, int device_ptrs);
  * launched in total (either pointer may be NULL). */
 glbm_status glbm_counters(glbm_t h, long long *steps, long long *launches);
 
+/*
+ * One FP32 time step plus the mean-velocity reduction, without allocating.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory themselves, such as applications whose host
+ * framework owns the whole device-memory budget and hands out every buffer,
+ * or pipelines that must not risk the implicit device synchronisation that
+ * cudaMalloc/cudaFree can cause in the middle of their loop.  It runs the
+ * same fused step kernel as glbm_step on buffers the caller owns; the
+ * kernel's reduction scratch (one FP64 pair per block, plus a 40-byte status)
+ * is a fixed 1 MiB array compiled into the library, held on every GPU that
+ * loads it until the process exits.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.
+ *
+ *   g_src   device, FP32 deviations g_i = f_i - w_i of the current
+ *           post-collision state, laid out [9][plane] (plane i holds node
+ *           y*nx + x), D2Q9 order as in glbm_get_distributions.  Read only.
+ *   g_dst   device, same layout, receives the state after the step; must not
+ *           overlap g_src.  Start from zeros for f_eq(rho = 1, u = 0).
+ *   alpha   device [ny][nx] FP32: eps*nu/K per node, nu = (tau - 1/2)/3
+ *           (0 for K = +inf).
+ *   eps     device [ny][nx] FP32 porosity.
+ *   beta    device [ny][nx] FP32 eps*F_eps/sqrt(K), or NULL for the paper's
+ *           Forchheimer-free model.
+ *   plane   elements per population plane: >= nx*ny and a multiple of 4;
+ *           every array must be 16-byte aligned.
+ *   flags   GLBM_WALLS_Y or GLBM_PERIODIC_Y.
+ *   mean_u  device, 2 doubles: receives (Ux, Uy) of this step.
+ *   stream  cudaStream_t (NULL = legacy default stream); all work is
+ *           enqueued on it and the call returns without waiting.
+ *
+ * Limit: the lattice may need at most 65536 reduction blocks, where one
+ * block covers 512 nodes of a row when nx is a multiple of 4 (else 128):
+ * e.g. 4096 x 8192 fits.  Larger lattices, misaligned arrays and other bad
+ * arguments return GLBM_EINVAL with a message in glbm_last_error(NULL).
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one scratch array, which
+ * keeps the last call's contents (the status is cleared at the start of each
+ * call): calls that overlap on the GPU, e.g. on two streams at once, race.
+ */
+glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst,
+                                     const float *alpha, const float *eps,
+                                     const float *beta, int nx, int ny,
+                                     long long plane, double tau, double gx,
+                                     double gy, unsigned flags,
+                                     double *mean_u, void *stream);
+
 /* Release all device memory of the handle.  NULL-safe. */
 void glbm_destroy(glbm_t h);
 
 /* Message of the last failure on this handle (h = NULL: the last failure of
- * glbm_create on this host thread).  Never NULL. */
+ * glbm_create or glbm_step_reduce_noalloc on this host thread).  Never NULL. */
 const char *glbm_last_error(glbm_t h);
 
 #ifdef __cplusplus

@@ -33,7 +33,8 @@ _STATUS = {0: "GLBM_OK", -1: "GLBM_EINVAL", -2: "GLBM_ENOMEM",
 SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_init_equilibrium", "glbm_step", "glbm_mean_velocity",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
-           "glbm_counters", "glbm_destroy", "glbm_last_error"]
+           "glbm_counters", "glbm_destroy", "glbm_last_error",
+           "glbm_step_reduce_noalloc"]
 
 
 class GLBMError(RuntimeError):
@@ -72,6 +73,8 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_counters": ([h, C.POINTER(ll), C.POINTER(ll)], i),
         "glbm_destroy": ([h], None),
         "glbm_last_error": ([h], C.c_char_p),
+        "glbm_step_reduce_noalloc": ([_VP, _VP, _VP, _VP, _VP, i, i, ll, d, d, d,
+                                      C.c_uint, _VP, _VP], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

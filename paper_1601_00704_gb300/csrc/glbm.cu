@@ -39,6 +39,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 namespace {
@@ -1058,3 +1059,129 @@ void glbm_destroy(glbm_t h) {
 const char *glbm_last_error(glbm_t h) { return h ? h->err : g_create_err; }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free step (glbm_step_reduce_noalloc).
+//
+// For callers that may not allocate device memory themselves: applications
+// whose host framework owns the whole device-memory budget and hands out
+// every buffer, or pipelines that must not risk the implicit device-wide
+// synchronisation that cudaMalloc/cudaFree can cause in the middle of their
+// loop.  The step kernel's only scratch (one FP64 partial pair per block plus
+// the reduction status) lives in the file-scope array below instead of a
+// per-handle allocation; every GPU that loads this library holds it until the
+// process exits.
+// ===========================================================================
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 65536;  // partial pairs: 1 MiB
+constexpr int kNoAllocStatusDoubles = 8;  // room for DevStatus (40 B)
+static_assert(sizeof(DevStatus) <= kNoAllocStatusDoubles * sizeof(double), "status slot");
+
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxBlocks + kNoAllocStatusDoubles];
+
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+// Failures are reported like glbm_create's: glbm_last_error(NULL).
+glbm_status noalloc_fail(glbm_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_err, sizeof(g_create_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+// Device address of the scratch array on the current device, looked up once
+// per device.  In host code the array's name is only a host-side stand-in,
+// never a device address, so it is never handed to a kernel directly.
+glbm_status noalloc_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(GLBM_EINVAL, "device ordinal %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        double *p = nullptr;
+        e = cudaGetSymbolAddress(reinterpret_cast<void **>(&p), g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return noalloc_fail(GLBM_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GLBM_OK;
+}
+
+template <int VEC, bool WALLS, bool FORCH>
+void noalloc_launch(const float *src, float *dst, const float *a, const float *e, const float *b, const Geo &geo,
+                    const Phys<float> &ph, double *partial, cudaStream_t st) {
+    const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
+    k_step<float, VEC, WALLS, FORCH, true><<<grid, kThreads, 0, st>>>(src, dst, a, e, b, geo, ph, partial);
+}
+
+}  // namespace
+
+extern "C" glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst, const float *alpha,
+                                                const float *eps, const float *beta, int nx, int ny,
+                                                long long plane, double tau, double gx, double gy,
+                                                unsigned flags, double *mean_u, void *stream) {
+    if (!g_src || !g_dst || !alpha || !eps || !mean_u)
+        return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: g_src, g_dst, alpha, eps and mean_u are required");
+    if (g_src == g_dst) return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: g_src and g_dst must differ");
+    if (nx < 2 || ny < 2 || (long long)nx * ny >= (1ll << 31))
+        return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: need nx, ny >= 2 and nx*ny < 2^31");
+    if (plane < (long long)nx * ny || plane % 4 != 0)
+        return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: plane must be >= nx*ny and a multiple of 4");
+    if (!(tau > 0.5) || !std::isfinite(tau) || !std::isfinite(gx) || !std::isfinite(gy))
+        return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: need finite tau > 1/2 and finite G");
+    if (flags & ~GLBM_PERIODIC_Y) return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: unknown flags");
+    const uintptr_t mis = (uintptr_t(g_src) | uintptr_t(g_dst) | uintptr_t(alpha) | uintptr_t(eps) |
+                           uintptr_t(beta)) & 15u;
+    if (mis) return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: arrays must be 16-byte aligned");
+    const int vec = (nx % 4 == 0) ? 4 : 1;
+    Geo geo;
+    geo.nx = nx;
+    geo.ny = ny;
+    geo.plane = plane;
+    geo.bpr = ((nx + vec - 1) / vec + kThreads - 1) / kThreads;
+    const long long blocks = (long long)geo.bpr * ny;
+    if (blocks > kNoAllocMaxBlocks)
+        return noalloc_fail(GLBM_EINVAL,
+                            "step_reduce_noalloc: lattice needs %lld reduction blocks but the fixed scratch "
+                            "holds %d (one block covers %d nodes of a row)",
+                            blocks, kNoAllocMaxBlocks, vec * kThreads);
+    double *scratch = nullptr;
+    if (glbm_status s = noalloc_scratch(&scratch)) return s;
+    double *partial = scratch;
+    DevStatus *st = reinterpret_cast<DevStatus *>(scratch + 2 * kNoAllocMaxBlocks);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    Phys<float> ph;
+    ph.omega = float(1.0 / tau);
+    ph.A = float(1.0 - 0.5 / tau);
+    ph.gx = float(gx);
+    ph.gy = float(gy);
+    ph.scale = 1.0f;
+    ph.inv_scale = 1.0f;
+    // the status keeps the previous call's values: start it from zero
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), cs);
+    if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    const bool walls = !(flags & GLBM_PERIODIC_Y), forch = beta != nullptr;
+    if (vec == 4) {
+        if (walls) forch ? noalloc_launch<4, true, true>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs)
+                         : noalloc_launch<4, true, false>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs);
+        else forch ? noalloc_launch<4, false, true>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs)
+                   : noalloc_launch<4, false, false>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs);
+    } else {
+        if (walls) forch ? noalloc_launch<1, true, true>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs)
+                         : noalloc_launch<1, true, false>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs);
+        else forch ? noalloc_launch<1, false, true>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs)
+                   : noalloc_launch<1, false, false>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs);
+    }
+    k_finalize<<<1, 256, 0, cs>>>(partial, int(blocks), 1.0 / double((long long)nx * ny), 0.0, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+    // DevStatus begins with (ux, uy)
+    e = cudaMemcpyAsync(mean_u, st, 2 * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+    if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+    return GLBM_OK;
+}
