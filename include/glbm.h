@@ -47,7 +47,15 @@ typedef enum {
 /* Storage precision of the distributions.  Collision arithmetic runs in
  * FP32 for the 32/16-bit formats and FP64 for GLBM_F64; the convergence
  * reduction always accumulates in FP64.  All formats store deviations
- * g_i = f_i - w_i * rho0 (rho0 = 1) rather than f_i. */
+ * g_i = f_i - w_i * rho0 (rho0 = 1) rather than f_i.  The 16-bit formats
+ * round stochastically by default (a counter-based hash of node, step and
+ * population decides each rounding direction, so runs are reproducible):
+ * nearest rounding freezes the slow pressure mode once its per-step change
+ * falls below half an ulp.  FP16 stores g*S with a power-of-two scale S that
+ * the library chooses from G (or the warm-start state) and then keeps the
+ * largest stored magnitude between 2^8 and 2^13, checked at the end of
+ * every chunk (so FP16 runs read a status back every chunk); BF16 has
+ * FP32's exponent range and stores g unscaled. */
 typedef enum {
     GLBM_F32 = 0,
     GLBM_F64 = 1,
@@ -58,12 +66,16 @@ typedef enum {
 /* Boundary flags (the paper states none; see glbm_create). */
 #define GLBM_WALLS_Y 0u    /* halfway bounce-back walls at y=-1/2, ny-1/2 */
 #define GLBM_PERIODIC_Y 1u /* periodic in y */
+/* 16-bit storage rounds to nearest instead of stochastically (for studies of
+ * the stagnation that nearest rounding causes; not recommended). */
+#define GLBM_NEAREST16 2u
 
 /*
  * Create a solver for an nx-by-ny lattice (x is always periodic).
  *   tau      BGK relaxation time (Eq. 29), must be > 1/2.
  *   storage  distribution storage format (above).
- *   flags    GLBM_WALLS_Y (default) or GLBM_PERIODIC_Y.
+ *   flags    GLBM_WALLS_Y (default) or GLBM_PERIODIC_Y, optionally or-ed
+ *            with GLBM_NEAREST16.
  *   stream   cudaStream_t to enqueue on; NULL = the legacy default stream.
  *   out      receives the handle.
  * Allocates both distribution buffers, the coefficient planes and the

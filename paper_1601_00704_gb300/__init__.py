@@ -20,11 +20,11 @@ import numpy as np
 from .build import LIB as LIB_PATH
 
 __all__ = ["Solver", "GLBMError", "load", "F32", "F64", "F16DEV", "BF16DEV",
-           "WALLS_Y", "PERIODIC_Y", "STORAGE"]
+           "WALLS_Y", "PERIODIC_Y", "NEAREST16", "STORAGE"]
 
 F32, F64, F16DEV, BF16DEV = 0, 1, 2, 3
 STORAGE = {"f32": F32, "f64": F64, "f16": F16DEV, "bf16": BF16DEV}
-WALLS_Y, PERIODIC_Y = 0, 1
+WALLS_Y, PERIODIC_Y, NEAREST16 = 0, 1, 2
 
 _STATUS = {0: "GLBM_OK", -1: "GLBM_EINVAL", -2: "GLBM_ENOMEM",
            -3: "GLBM_ECUDA", -4: "GLBM_ENAN", -5: "GLBM_ESTATE"}
@@ -130,10 +130,12 @@ class Solver:
     ``storage`` is 'f32' (default), 'f64', 'f16' or 'bf16'; ``walls`` puts
     halfway bounce-back walls at y = -1/2 and ny - 1/2 (else periodic y);
     ``stream`` is a ``torch.cuda.Stream`` (or raw cudaStream_t int), default
-    the legacy default stream.
+    the legacy default stream; ``flags`` adds further ``glbm_create`` flags
+    (``NEAREST16``).
     """
 
-    def __init__(self, nx, ny, tau=1.0, storage="f32", walls=True, stream=None):
+    def __init__(self, nx, ny, tau=1.0, storage="f32", walls=True, stream=None,
+                 flags=0):
         self._lib = load()
         self._h = _VP()
         self.nx, self.ny, self.tau = int(nx), int(ny), float(tau)
@@ -143,7 +145,7 @@ class Solver:
             s = s.cuda_stream
         self._stream = s
         rc = self._lib.glbm_create(self.nx, self.ny, self.tau, st,
-                                   WALLS_Y if walls else PERIODIC_Y,
+                                   (WALLS_Y if walls else PERIODIC_Y) | int(flags),
                                    _VP(s) if s else None, C.byref(self._h))
         if rc != 0:
             raise GLBMError(rc, self._lib.glbm_last_error(None).decode())

@@ -84,27 +84,71 @@ __device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
 // ---------------------------------------------------------------------------
 // Storage formats.  R is the collision arithmetic type.
 // ---------------------------------------------------------------------------
+// Stochastic rounding: round |x| up with probability equal to the dropped
+// fraction, using uniform random bits r; unbiased in expectation, so slow
+// modes whose per-step change is below half an ulp do not freeze.
+__device__ __forceinline__ __half f2h_sr(float x, uint32_t r) {
+    const float a = fabsf(x);
+    if (!(a < 65504.0f)) return __float2half_rn(x);  // overflow, inf, NaN
+    if (a >= 6.103515625e-05f) {                      // FP16 normal: drop 13 mantissa bits
+        const uint32_t b = (__float_as_uint(x) + (r & 0x1FFFu)) & ~0x1FFFu;
+        return __float2half_rz(__uint_as_float(b));   // exact
+    }
+    // FP16 subnormal range: fixed quantum 2^-24
+    const float q = floorf(fmaf(a, 16777216.0f, float(r & 0xFFFFu) * (1.0f / 65536.0f)));
+    return __float2half_rn(copysignf(q * 5.9604644775390625e-08f, x));
+}
+__device__ __forceinline__ __nv_bfloat16 f2bf_sr(float x, uint32_t r) {
+    if (!(fabsf(x) < 3.38e38f)) return __float2bfloat16_rn(x);
+    const uint32_t b = (__float_as_uint(x) + (r & 0xFFFFu)) & 0xFFFF0000u;  // drop 16 bits
+    return __float2bfloat16_rz(__uint_as_float(b));                         // exact
+}
+
 template <typename T> struct Store;
 template <> struct Store<float> {
     using R = float;
+    static constexpr bool kSmall = false;
     __device__ static float ld(float v, float) { return v; }
     __device__ static float st(float v, float) { return v; }
+    __device__ static float st_sr(float v, float, uint32_t) { return v; }
 };
 template <> struct Store<double> {
     using R = double;
+    static constexpr bool kSmall = false;
     __device__ static double ld(double v, double) { return v; }
     __device__ static double st(double v, double) { return v; }
+    __device__ static double st_sr(double v, double, uint32_t) { return v; }
 };
 template <> struct Store<__half> {
     using R = float;
+    static constexpr bool kSmall = true;
     __device__ static float ld(__half v, float inv_s) { return __half2float(v) * inv_s; }
     __device__ static __half st(float v, float s) { return __float2half_rn(v * s); }
+    __device__ static __half st_sr(float v, float s, uint32_t r) { return f2h_sr(v * s, r); }
 };
 template <> struct Store<__nv_bfloat16> {
     using R = float;
+    static constexpr bool kSmall = true;
     __device__ static float ld(__nv_bfloat16 v, float inv_s) { return __bfloat162float(v) * inv_s; }
     __device__ static __nv_bfloat16 st(float v, float s) { return __float2bfloat16_rn(v * s); }
+    __device__ static __nv_bfloat16 st_sr(float v, float s, uint32_t r) { return f2bf_sr(v * s, r); }
 };
+
+// Nodes per thread: 16-byte vectors for 32/64-bit storage, 8-byte vectors
+// (4 nodes) for 16-bit storage.
+template <typename T>
+constexpr int kVecOf = sizeof(T) == 2 ? 4 : int(16 / sizeof(T));
+
+// Integer hash ("lowbias32" multiply-xorshift) for the stochastic rounding
+// bits: one 32-bit word per (node, step, population pair).
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 template <typename R>
 struct Phys {
@@ -113,6 +157,8 @@ struct Phys {
     R gx, gy;    // external force G
     R scale;     // storage scale S (stored = g*S); 1 for FP32/FP64
     R inv_scale; // 1/S
+    uint32_t step_key;  // per-step key of the stochastic-rounding hash
+    int sr;             // 16-bit storage: 1 = stochastic rounding, 0 = nearest
 };
 
 struct Geo {
@@ -121,23 +167,36 @@ struct Geo {
     int bpr;          // blocks per row
 };
 
-// 16-byte vector moves.
+// Vector moves of 8 bytes or a multiple of 16 bytes.
 template <typename X, int N>
 __device__ __forceinline__ void ld16(const X *__restrict__ p, X (&out)[N]) {
-    static_assert((N * sizeof(X)) % 16 == 0, "16-byte multiple");
+    constexpr int B = int(N * sizeof(X));
+    static_assert(B == 8 || B % 16 == 0, "8-byte or 16-byte multiple");
+    if constexpr (B == 8) {
+        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        memcpy(&out[0], &u, 8);
+    } else {
 #pragma unroll
-    for (int j = 0; j < int(N * sizeof(X) / 16); ++j) {
-        uint4 u = reinterpret_cast<const uint4 *>(p)[j];
-        memcpy(&out[j * (16 / sizeof(X))], &u, 16);
+        for (int j = 0; j < B / 16; ++j) {
+            uint4 u = reinterpret_cast<const uint4 *>(p)[j];
+            memcpy(&out[j * (16 / sizeof(X))], &u, 16);
+        }
     }
 }
 template <typename X, int N>
 __device__ __forceinline__ void st16(X *__restrict__ p, const X (&in)[N]) {
+    constexpr int B = int(N * sizeof(X));
+    if constexpr (B == 8) {
+        uint2 u;
+        memcpy(&u, &in[0], 8);
+        __stcs(reinterpret_cast<uint2 *>(p), u);
+    } else {
 #pragma unroll
-    for (int j = 0; j < int(N * sizeof(X) / 16); ++j) {
-        uint4 u;
-        memcpy(&u, &in[j * (16 / sizeof(X))], 16);
-        __stcs(reinterpret_cast<uint4 *>(p) + j, u);
+        for (int j = 0; j < B / 16; ++j) {
+            uint4 u;
+            memcpy(&u, &in[j * (16 / sizeof(X))], 16);
+            __stcs(reinterpret_cast<uint4 *>(p) + j, u);
+        }
     }
 }
 
@@ -336,15 +395,29 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
 
 constexpr int kThreads = 128;
 
+// Block maximum of a non-negative float; thread 0 returns it.
+__device__ __forceinline__ float block_max(float m) {
+    __shared__ float shm[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) shm[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmaxf(m, shm[w]);
+    return m;
+}
+
 // ---------------------------------------------------------------------------
 // K2: fused pull-stream + collide (one time step).  REDUCE additionally
-// writes this block's FP64 sums of u_x, u_y to partial[2*block].
+// writes this block's FP64 sums of u_x, u_y to partial[2*block] and, for
+// 16-bit storage, the largest stored magnitude |g*S| to pmax[block].
 // ---------------------------------------------------------------------------
 template <typename T, int VEC, bool WALLS, bool FORCH, bool REDUCE>
 __global__ void __launch_bounds__(kThreads)
 k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::R *__restrict__ alpha,
        const typename Store<T>::R *__restrict__ epsv, const typename Store<T>::R *__restrict__ betav,
-       Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ partial) {
+       Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ partial, float *__restrict__ pmax) {
     using R = typename Store<T>::R;
     const int y = blockIdx.x / geo.bpr;
     const int bx = blockIdx.x - y * geo.bpr;
@@ -374,12 +447,30 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
             sy += double(uy);
         }
     }
+    float gm = 0.0f;
     if (active) {
+        uint32_t hk[VEC];
+        if constexpr (Store<T>::kSmall) {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) hk[k] = mix32(uint32_t(n0 + k) ^ ph.step_key);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             T v[VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = Store<T>::st(g[k][i], ph.scale);
+            for (int k = 0; k < VEC; ++k) {
+                if constexpr (Store<T>::kSmall) {
+                    if (ph.sr) {
+                        uint32_t r = mix32(hk[k] + uint32_t(i >> 1) * 0x9E3779B9u);
+                        v[k] = Store<T>::st_sr(g[k][i], ph.scale, (i & 1) ? (r >> 16) : r);
+                    } else {
+                        v[k] = Store<T>::st(g[k][i], ph.scale);
+                    }
+                    if (REDUCE) gm = fmaxf(gm, fabsf(float(v[k])));
+                } else {
+                    v[k] = Store<T>::st(g[k][i], ph.scale);
+                }
+            }
             T *p = dst + (long long)i * geo.plane + n0;
             if constexpr (VEC == 1) p[0] = v[0];
             else st16<T, VEC>(p, v);
@@ -391,6 +482,10 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
             partial[2ll * blockIdx.x] = sx;
             partial[2ll * blockIdx.x + 1] = sy;
         }
+        if constexpr (Store<T>::kSmall) {
+            gm = block_max(gm);
+            if (threadIdx.x == 0) pmax[blockIdx.x] = gm;
+        }
     }
 }
 
@@ -401,21 +496,24 @@ struct DevStatus {
     int have_prev;     // prev_ux valid
     int converged;     // set by the last finalize
     int nonfinite;     // mean velocity not finite
-    int pad;
+    float gmax;        // 16-bit storage: largest stored |g*S| at that step
 };
 
 // K3 finalize: fixed-order FP64 sum of the block partials, mean, test.
 __global__ void __launch_bounds__(256)
 k_finalize(const double *__restrict__ partial, int nparts, double inv_n, double tol,
-           DevStatus *__restrict__ st) {
+           DevStatus *__restrict__ st, const float *__restrict__ pmax) {
     __shared__ double sh[2][256];
     double a = 0.0, b = 0.0;
+    float m = 0.0f;
     for (int j = threadIdx.x; j < nparts; j += 256) {
         a += partial[2ll * j];
         b += partial[2ll * j + 1];
+        if (pmax) m = fmaxf(m, pmax[j]);
     }
     sh[0][threadIdx.x] = a;
     sh[1][threadIdx.x] = b;
+    if (pmax) m = block_max(m);
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
@@ -434,6 +532,7 @@ k_finalize(const double *__restrict__ partial, int nparts, double inv_n, double 
                          fabs(ux - st->prev_ux) <= tol * fabs(ux)) ? 1 : 0;
         st->prev_ux = ux;
         st->have_prev = 1;
+        st->gmax = m;
     }
 }
 
@@ -501,6 +600,37 @@ __global__ void k_init_eq(T *__restrict__ dst, long long plane, long long N,
     }
 }
 
+// Largest |f_eq - w| over nodes and populations (for choosing the FP16
+// scale before a warm start); float bits of a non-negative value order like
+// the integers, so atomicMax on them is a float max.
+__global__ void k_eq_max(long long N, const float *__restrict__ epsv, const double *__restrict__ rho,
+                         const double *__restrict__ ux, const double *__restrict__ uy, int *__restrict__ out) {
+    float m = 0.0f;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const double r = rho ? rho[n] : 1.0;
+        const double vx = ux ? ux[n] : 0.0, vy = uy ? uy[n] : 0.0;
+        const double ie = 1.0 / double(epsv[n]);
+        const double uu = vx * vx + vy * vy;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double eu = cx(i) * vx + cy(i) * vy;
+            const double w = wgt<double>(i);
+            const double gdev = w * (r - 1.0) + w * r * (3.0 * eu + 4.5 * ie * eu * eu - 1.5 * ie * uu);
+            m = fmaxf(m, float(fabs(gdev)));
+        }
+    }
+    atomicMax(out, __float_as_int(m));
+}
+
+// Multiply every stored value by a power of two (FP16 scale change).
+template <typename T>
+__global__ void k_rescale(T *__restrict__ buf, long long count, float factor) {
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < count;
+         n += (long long)gridDim.x * blockDim.x)
+        buf[n] = Store<T>::st(Store<T>::ld(buf[n], 1.0f) * factor, 1.0f);
+}
+
 // Velocity export: re-run the step's gather and velocity solve on the
 // pre-step state (scalar loads; same arithmetic as k_step).
 template <typename T, bool WALLS, bool FORCH>
@@ -557,6 +687,7 @@ struct glbm {
     int cur = 0;         // buffer holding the current state
     void *coef[3] = {nullptr, nullptr, nullptr};  // alpha, eps, beta
     double *partial = nullptr;
+    float *pmax = nullptr;  // 16-bit storage: block maxima of |stored|
     int nparts_max = 0;
     DevStatus *dstat = nullptr;
     DevStatus *hstat = nullptr;  // pinned
@@ -564,7 +695,11 @@ struct glbm {
     double *stage = nullptr;  // 3*N doubles of input staging, allocated on first host input
     bool has_medium = false, forch = false, reduced = false;
     double feps_mode = 0.0, gx = 0.0, gy = 0.0;
-    double scale = 1.0;
+    double scale = 1.0;       // FP16 storage scale S (stored = g*S)
+    bool sr = true;           // 16-bit storage: stochastic rounding
+    bool at_rest = false;     // state is f_eq(1, 0) (zero deviations)
+    uint32_t seed = 0x2545F491u;
+    long long tstep = 0;      // time steps launched since the last reset
     long long steps = 0, launches = 0;
     char err[512] = "";
 };
@@ -589,7 +724,7 @@ glbm_status fail(glbm *h, glbm_status s, const char *fmt, ...) {
     } while (0)
 
 int vec_width(const glbm *h) {
-    const int v = int(16 / h->elem);
+    const int v = h->elem == 2 ? 4 : int(16 / h->elem);
     return (h->nx % v == 0) ? v : 1;
 }
 
@@ -612,6 +747,8 @@ Phys<R> make_phys(const glbm *h) {
     p.gy = R(h->gy);
     p.scale = R(h->scale);
     p.inv_scale = R(1.0 / h->scale);
+    p.step_key = mix32(uint32_t(h->tstep) * 0x9E3779B9u + h->seed);
+    p.sr = h->sr ? 1 : 0;
     return p;
 }
 
@@ -632,17 +769,20 @@ glbm_status launch_step_t(glbm *h, bool reduce) {
     const R *b = static_cast<const R *>(h->coef[2]);
     const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
     if (reduce)
-        k_step<T, VEC, WALLS, FORCH, true><<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial);
+        k_step<T, VEC, WALLS, FORCH, true>
+            <<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial, h->pmax);
     else
-        k_step<T, VEC, WALLS, FORCH, false><<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial);
+        k_step<T, VEC, WALLS, FORCH, false>
+            <<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial, h->pmax);
     h->launches++;
+    h->tstep++;
     h->cur ^= 1;
     return GLBM_OK;
 }
 
 template <typename T>
 glbm_status launch_step(glbm *h, bool reduce) {
-    constexpr int V = int(16 / sizeof(T));
+    constexpr int V = kVecOf<T>;
     const bool walls = !(h->flags & GLBM_PERIODIC_Y);
     const bool vec = vec_width(h) > 1;
     if (vec) {
@@ -669,7 +809,8 @@ int nparts(const glbm *h) {
 }
 
 glbm_status finalize(glbm *h, double tol) {
-    k_finalize<<<1, 256, 0, h->stream>>>(h->partial, nparts(h), 1.0 / double(h->N), tol, h->dstat);
+    k_finalize<<<1, 256, 0, h->stream>>>(h->partial, nparts(h), 1.0 / double(h->N), tol, h->dstat,
+                                         h->elem == 2 ? h->pmax : nullptr);
     h->launches++;
     h->reduced = true;
     return GLBM_OK;
@@ -685,6 +826,37 @@ glbm_status reset_status(glbm *h) {
     CU(h, cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), h->stream));
     h->reduced = false;
     return GLBM_OK;
+}
+
+double pow2_floor(double x) { return std::ldexp(1.0, int(std::floor(std::log2(x)))); }
+
+// FP16 scale that puts a deviation bound `gbound` near 2^12 (FP16 normal
+// range is 2^-14 .. 65504, relative precision 2^-11 throughout).
+double fp16_scale_for(double gbound) {
+    if (!(gbound > 0.0) || !std::isfinite(gbound)) return 1.0;
+    return std::fmin(std::fmax(pow2_floor(4096.0 / gbound), 0x1p-24), 0x1p64);
+}
+
+template <typename T>
+void rescale_t(glbm *h, float factor) {
+    for (int b = 0; b < 2; ++b) {
+        k_rescale<T><<<grid_1d(9 * h->plane), 256, 0, h->stream>>>(static_cast<T *>(h->buf[b]), 9 * h->plane,
+                                                                   factor);
+        h->launches++;
+    }
+}
+
+// Keep the largest stored FP16 magnitude between 2^8 and 2^13: rescale both
+// buffers by a power of two when the last reduction saw it outside.
+void adapt_fp16_scale(glbm *h, float gmax) {
+    if (h->storage != GLBM_F16DEV || !(gmax >= 0.0f)) return;
+    int k = 0;
+    if (gmax > 8192.0f) k = -int(std::ceil(std::log2(double(gmax) / 4096.0)));
+    else if (gmax > 0.0f && gmax < 256.0f) k = int(std::floor(std::log2(4096.0 / double(gmax))));
+    if (k == 0) return;
+    const float factor = float(std::ldexp(1.0, k));
+    rescale_t<__half>(h, factor);
+    h->scale *= double(factor);
 }
 
 template <typename T>
@@ -787,6 +959,7 @@ void release(glbm *h) {
     for (auto &p : h->buf) if (p) cudaFree(p), p = nullptr;
     for (auto &p : h->coef) if (p) cudaFree(p), p = nullptr;
     if (h->partial) cudaFree(h->partial), h->partial = nullptr;
+    if (h->pmax) cudaFree(h->pmax), h->pmax = nullptr;
     if (h->dstat) cudaFree(h->dstat), h->dstat = nullptr;
     if (h->dflag) cudaFree(h->dflag), h->dflag = nullptr;
     if (h->stage) cudaFree(h->stage), h->stage = nullptr;
@@ -810,7 +983,8 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
         return fail(nullptr, GLBM_EINVAL, "glbm_create: tau must be a finite value > 1/2 (got %g)", tau);
     if (storage != GLBM_F32 && storage != GLBM_F64 && storage != GLBM_F16DEV && storage != GLBM_BF16DEV)
         return fail(nullptr, GLBM_EINVAL, "glbm_create: unknown storage %d", int(storage));
-    if (flags & ~GLBM_PERIODIC_Y) return fail(nullptr, GLBM_EINVAL, "glbm_create: unknown flags 0x%x", flags);
+    if (flags & ~(GLBM_PERIODIC_Y | GLBM_NEAREST16))
+        return fail(nullptr, GLBM_EINVAL, "glbm_create: unknown flags 0x%x", flags);
     glbm *h = new (std::nothrow) glbm;
     if (!h) return fail(nullptr, GLBM_ENOMEM, "glbm_create: out of host memory");
     h->nx = nx;
@@ -823,6 +997,7 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
     h->stream = static_cast<cudaStream_t>(stream);
     h->elem = storage == GLBM_F64 ? 8 : (storage == GLBM_F32 ? 4 : 2);
     h->celem = storage == GLBM_F64 ? 8 : 4;
+    h->sr = !(flags & GLBM_NEAREST16);
     cudaError_t e = cudaGetDevice(&h->dev);
     const size_t fbytes = size_t(9) * h->plane * h->elem;
     const size_t cbytes = size_t(h->plane) * h->celem;
@@ -833,6 +1008,7 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
     if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], fbytes);
     for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMalloc(&h->coef[c], cbytes);
     if (e == cudaSuccess) e = cudaMalloc(&h->partial, sizeof(double) * 2 * size_t(h->nparts_max));
+    if (e == cudaSuccess) e = cudaMalloc(&h->pmax, sizeof(float) * size_t(h->nparts_max));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstat, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&h->hstat, sizeof(DevStatus));
@@ -880,6 +1056,9 @@ glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K, double
     if (glbm_status s = reset_status(h)) return s;
     h->cur = 0;
     h->steps = 0;
+    h->tstep = 0;
+    h->at_rest = true;
+    if (h->storage == GLBM_F16DEV) h->scale = fp16_scale_for(16.0 * (std::fabs(h->gx) + std::fabs(h->gy)));
     h->has_medium = true;
     h->feps_mode = F_eps;
     h->forch = F_eps != 0.0;
@@ -891,6 +1070,10 @@ glbm_status glbm_set_force(glbm_t h, double gx, double gy) {
     if (!std::isfinite(gx) || !std::isfinite(gy)) return fail(h, GLBM_EINVAL, "set_force: G must be finite");
     h->gx = gx;
     h->gy = gy;
+    // FP16 at rest: start with |g*S| ~ 2^8 per unit of G (the first steps'
+    // deviations are O(eps*G)); later chunks adapt S to the stored maximum
+    if (h->storage == GLBM_F16DEV && h->at_rest && (gx != 0.0 || gy != 0.0))
+        h->scale = fp16_scale_for(16.0 * (std::fabs(gx) + std::fabs(gy)));
     // clear the convergence history but keep the last mean velocity
     CU(h, cudaMemsetAsync(&h->dstat->have_prev, 0, sizeof(int), h->stream));
     return GLBM_OK;
@@ -916,11 +1099,25 @@ glbm_status glbm_init_equilibrium(glbm_t h, const double *rho, const double *ux,
             return fail(h, GLBM_EINVAL, "init_equilibrium: node %d has rho = %g, u = (%g, %g)", bad,
                         fetch(h, d[0], bad), fetch(h, d[1], bad), fetch(h, d[2], bad));
     }
+    if (h->storage == GLBM_F16DEV) {
+        int mbits = 0;
+        CU(h, cudaMemsetAsync(h->dflag, 0, sizeof(int), h->stream));
+        k_eq_max<<<grid_1d(N), 256, 0, h->stream>>>(N, static_cast<const float *>(h->coef[1]), d[0], d[1], d[2],
+                                                     h->dflag);
+        h->launches++;
+        if (glbm_status s = read_flag(h, &mbits)) return s;
+        float m;
+        memcpy(&m, &mbits, sizeof(m));
+        if (m > 0.0f) h->scale = fp16_scale_for(double(m));
+        else h->scale = fp16_scale_for(16.0 * (std::fabs(h->gx) + std::fabs(h->gy)));
+    }
     h->cur = 0;
     init_eq_dispatch(h, d[0], d[1], d[2]);
     if (glbm_status s = launch_error(h)) return s;
     if (glbm_status s = reset_status(h)) return s;
     h->steps = 0;
+    h->tstep = 0;
+    h->at_rest = !(rho || ux);
     return GLBM_OK;
 }
 
@@ -935,11 +1132,13 @@ glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every, long l
     long long done = 0;
     int conv = 0;
     const bool test = tol > 0.0;
+    const bool adapt = h->storage == GLBM_F16DEV;
+    if (n > 0) h->at_rest = false;
     while (done < n) {
         long long chunk = n - done;
         if (chunk > check_every) chunk = check_every;
         const bool last_chunk = done + chunk == n;
-        const bool reduce_here = test || last_chunk;
+        const bool reduce_here = test || last_chunk || adapt;
         for (long long s = 0; s < chunk; ++s) {
             glbm_status st = do_step(h, reduce_here && s == chunk - 1);
             if (st) return st;
@@ -948,13 +1147,15 @@ glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every, long l
         h->steps += chunk;
         if (reduce_here) finalize(h, test ? tol : 0.0);
         if (glbm_status st = launch_error(h)) return st;
-        if (test) {
+        if (test || adapt) {
             if (glbm_status st = read_status(h)) return st;
             if (h->hstat->nonfinite) {
                 if (steps_done) *steps_done = done;
                 return fail(h, GLBM_ENAN, "step: non-finite mean velocity after %lld steps", h->steps);
             }
-            if (h->hstat->converged) {
+            adapt_fp16_scale(h, h->hstat->gmax);
+            if (glbm_status st = launch_error(h)) return st;
+            if (test && h->hstat->converged) {
                 conv = 1;
                 break;
             }
@@ -1116,7 +1317,7 @@ template <int VEC, bool WALLS, bool FORCH>
 void noalloc_launch(const float *src, float *dst, const float *a, const float *e, const float *b, const Geo &geo,
                     const Phys<float> &ph, double *partial, cudaStream_t st) {
     const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
-    k_step<float, VEC, WALLS, FORCH, true><<<grid, kThreads, 0, st>>>(src, dst, a, e, b, geo, ph, partial);
+    k_step<float, VEC, WALLS, FORCH, true><<<grid, kThreads, 0, st>>>(src, dst, a, e, b, geo, ph, partial, nullptr);
 }
 
 }  // namespace
@@ -1162,6 +1363,8 @@ extern "C" glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst
     ph.gy = float(gy);
     ph.scale = 1.0f;
     ph.inv_scale = 1.0f;
+    ph.step_key = 0;
+    ph.sr = 0;
     // the status keeps the previous call's values: start it from zero
     cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), cs);
     if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
@@ -1177,7 +1380,7 @@ extern "C" glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst
         else forch ? noalloc_launch<1, false, true>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs)
                    : noalloc_launch<1, false, false>(g_src, g_dst, alpha, eps, beta, geo, ph, partial, cs);
     }
-    k_finalize<<<1, 256, 0, cs>>>(partial, int(blocks), 1.0 / double((long long)nx * ny), 0.0, st);
+    k_finalize<<<1, 256, 0, cs>>>(partial, int(blocks), 1.0 / double((long long)nx * ny), 0.0, st, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(GLBM_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
     // DevStatus begins with (ux, uy)
