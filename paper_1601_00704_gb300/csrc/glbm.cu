@@ -80,6 +80,10 @@ __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
+// Reciprocals of rho ~ 1, 2*c0 >= 1 and eps in (0, 1]: the hardware
+// approximation (within 1 ulp) is ample and a fraction of IEEE rcp's cost.
+__device__ __forceinline__ float rrcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
 
 // ---------------------------------------------------------------------------
 // Storage formats.  R is the collision arithmetic type.
@@ -87,21 +91,22 @@ __device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
 // Stochastic rounding: round |x| up with probability equal to the dropped
 // fraction, using uniform random bits r; unbiased in expectation, so slow
 // modes whose per-step change is below half an ulp do not freeze.
+// FP16: stochastic in the normal range [2^-14, 65504]; values below it are
+// rounded to nearest -- with the scale keeping the largest stored magnitude
+// near 2^12 they lie 2^26 below it, where a biased last bit is immaterial --
+// and overflow, inf and NaN convert as usual.
 __device__ __forceinline__ __half f2h_sr(float x, uint32_t r) {
-    const float a = fabsf(x);
-    if (!(a < 65504.0f)) return __float2half_rn(x);  // overflow, inf, NaN
-    if (a >= 6.103515625e-05f) {                      // FP16 normal: drop 13 mantissa bits
-        const uint32_t b = (__float_as_uint(x) + (r & 0x1FFFu)) & ~0x1FFFu;
-        return __float2half_rz(__uint_as_float(b));   // exact
-    }
-    // FP16 subnormal range: fixed quantum 2^-24
-    const float q = floorf(fmaf(a, 16777216.0f, float(r & 0xFFFFu) * (1.0f / 65536.0f)));
-    return __float2half_rn(copysignf(q * 5.9604644775390625e-08f, x));
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t a = b & 0x7fffffffu;
+    const uint32_t t = (b + (r & 0x1FFFu)) & ~0x1FFFu;  // drop 13 mantissa bits
+    const bool normal = a - 0x38800000u < 0x477fe000u - 0x38800000u;
+    return normal ? __float2half_rz(__uint_as_float(t)) : __float2half_rn(x);
 }
 __device__ __forceinline__ __nv_bfloat16 f2bf_sr(float x, uint32_t r) {
-    if (!(fabsf(x) < 3.38e38f)) return __float2bfloat16_rn(x);
-    const uint32_t b = (__float_as_uint(x) + (r & 0xFFFFu)) & 0xFFFF0000u;  // drop 16 bits
-    return __float2bfloat16_rz(__uint_as_float(b));                         // exact
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t t = (b + (r & 0xFFFFu)) & 0xFFFF0000u;  // drop 16 mantissa bits
+    const bool finite = (b & 0x7f800000u) != 0x7f800000u;
+    return finite ? __float2bfloat16_rz(__uint_as_float(t)) : __float2bfloat16_rn(x);
 }
 
 template <typename T> struct Store;
@@ -125,13 +130,28 @@ template <> struct Store<__half> {
     __device__ static float ld(__half v, float inv_s) { return __half2float(v) * inv_s; }
     __device__ static __half st(float v, float s) { return __float2half_rn(v * s); }
     __device__ static __half st_sr(float v, float s, uint32_t r) { return f2h_sr(v * s, r); }
+    static constexpr bool kScaled = true;
+    // Two scaled values -> packed pair with hardware stochastic rounding
+    // (cvt.rs): `lo` lands in the low half (lower address), `hi` in the high.
+    __device__ static uint32_t pack_sr(float lo, float hi, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+        return d;
+    }
 };
 template <> struct Store<__nv_bfloat16> {
     using R = float;
     static constexpr bool kSmall = true;
-    __device__ static float ld(__nv_bfloat16 v, float inv_s) { return __bfloat162float(v) * inv_s; }
-    __device__ static __nv_bfloat16 st(float v, float s) { return __float2bfloat16_rn(v * s); }
-    __device__ static __nv_bfloat16 st_sr(float v, float s, uint32_t r) { return f2bf_sr(v * s, r); }
+    // BF16 has FP32's exponent range: stored unscaled (the scale is always 1)
+    __device__ static float ld(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+    __device__ static __nv_bfloat16 st(float v, float) { return __float2bfloat16_rn(v); }
+    __device__ static __nv_bfloat16 st_sr(float v, float, uint32_t r) { return f2bf_sr(v, r); }
+    static constexpr bool kScaled = false;
+    __device__ static uint32_t pack_sr(float lo, float hi, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+        return d;
+    }
 };
 
 // Nodes per thread: 16-byte vectors for 32/64-bit storage, 8-byte vectors
@@ -214,7 +234,7 @@ __device__ __forceinline__ void node_velocity(const R (&g)[9], R alpha, R eps, R
     const R mx = radd(radd(rsub(g[1], g[3]), rsub(g[5], g[7])), rsub(g[8], g[6]));
     const R my = radd(radd(rsub(g[2], g[4]), rsub(g[5], g[7])), rsub(g[6], g[8]));
     const R rho = radd(R(1), drho);
-    const R inv_rho = rdiv(R(1), rho);
+    const R inv_rho = rrcp(rho);
     const R heps = rmul(R(0.5), eps);
     const R vx = rfma(mx, inv_rho, rmul(heps, ph.gx));
     const R vy = rfma(my, inv_rho, rmul(heps, ph.gy));
@@ -227,16 +247,44 @@ __device__ __forceinline__ void node_velocity(const R (&g)[9], R alpha, R eps, R
     } else {
         den = rfma(R(0.5), alpha, R(1));  // 2*c0
     }
-    const R inv_den = rdiv(R(1), den);
+    const R inv_den = rrcp(den);
     ux = rmul(vx, inv_den);
     uy = rmul(vy, inv_den);
 }
 
 // Eq. 27 force, Eq. 30 equilibrium and Eq. 31 forcing (with the 1/eps on the
-// u.F term, the mass-conserving reading), then the BGK update of Eq. 29.
-// g[] holds the streamed deviations on entry and the post-collision
-// deviations on exit.
-template <typename R, bool FORCH>
+// u.F term, the mass-conserving reading), then the BGK update of Eq. 29,
+// g* = g + (g_eq - g)/tau + F_i.
+//
+// Rounding: at Darcy velocities every deviation is dominated by its density
+// carrier w_i (rho - 1), several decades above the velocity terms.  The update
+// is therefore regrouped as
+//     g* = w d + [ (1 - 1/tau)(g - w d) + w (even +- odd) ],   d = rho - 1,
+// where the bracket holds only small terms (g - w d is exact when g ~ w d),
+// so the carrier is rounded twice per population instead of at every term.
+// Opposite directions share the even part of f_eq and F_i (terms in 1,
+// (e.u)^2, (e.u)(e.F)) and flip the odd part (e.u, e.F).  g[] holds the
+// streamed deviations on entry and the post-collision deviations on exit.
+template <typename R, bool CARRIER>
+__device__ __forceinline__ void collide_pair(R &gi, R &gj, R w, R wd, R eu, R eF, R k1, R om, R su, R a2,
+                                             R rho3, R fb, R f3, R f9) {
+    // even:  om [rho (9/(2 eps)(e.u)^2 - 3/(2 eps) u^2)] + rho A [9/eps (e.u)(e.F) - 3/eps u.F]
+    // odd :  om [3 rho e.u] + rho A [3 e.F]
+    const R ev = om * (a2 * eu * eu - su) + (fb + f9 * eu * eF);
+    const R od = om * rho3 * eu + f3 * eF;
+    if (CARRIER) {
+        gi = wd + (k1 * (gi - wd) + w * (ev + od));
+        gj = wd + (k1 * (gj - wd) + w * (ev - od));
+    } else {
+        // 16-bit storage: its own rounding dominates, use the shorter form
+        // k1 g + om w d + w (even +- odd)
+        const R b = om * wd;
+        gi = k1 * gi + (b + w * (ev + od));
+        gj = k1 * gj + (b + w * (ev - od));
+    }
+}
+
+template <typename R, bool FORCH, bool CARRIER = true>
 __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
                                         const Phys<R> &ph, R &ux, R &uy) {
     R drho;
@@ -249,20 +297,23 @@ __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
         Fx -= bu * ux;
         Fy -= bu * uy;
     }
-    const R inv_eps = R(1) / eps;
-    const R tu = R(1.5) * inv_eps * (ux * ux + uy * uy);
-    const R tF = R(3) * inv_eps * (ux * Fx + uy * Fy);
+    const R ie = rrcp(eps);
+    const R om = ph.omega, k1 = R(1) - ph.omega;
+    const R rho3 = R(3) * rho;
+    const R a2 = R(4.5) * ie * rho;
+    const R su = R(1.5) * ie * rho * (ux * ux + uy * uy);
     const R rA = rho * ph.A;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const R eu = R(cx(i)) * ux + R(cy(i)) * uy;
-        const R eF = R(cx(i)) * Fx + R(cy(i)) * Fy;
-        const R w = wgt<R>(i);
-        // f_eq_i - w_i = w_i (rho - 1) + w_i rho [3 e.u + 9/(2 eps)(e.u)^2 - 3/(2 eps) u^2]
-        const R geq = w * (drho + rho * (R(3) * eu + R(4.5) * inv_eps * eu * eu - tu));
-        const R Fi = w * rA * (R(3) * eF + R(9) * inv_eps * eu * eF - tF);
-        g[i] = g[i] + ph.omega * (geq - g[i]) + Fi;
-    }
+    const R f3 = R(3) * rA;
+    const R f9 = R(9) * ie * rA;
+    const R fb = R(-3) * ie * rA * (ux * Fx + uy * Fy);
+    const R w0 = wgt<R>(0), w1 = wgt<R>(1), w2 = wgt<R>(5);
+    const R wd0 = w0 * drho, wd1 = w1 * drho, wd2 = w2 * drho;
+    if (CARRIER) g[0] = wd0 + (k1 * (g[0] - wd0) + w0 * (fb - om * su));
+    else g[0] = k1 * g[0] + (om * wd0 + w0 * (fb - om * su));
+    collide_pair<R, CARRIER>(g[1], g[3], w1, wd1, ux, Fx, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R, CARRIER>(g[2], g[4], w1, wd1, uy, Fy, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R, CARRIER>(g[5], g[7], w2, wd2, ux + uy, Fx + Fy, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R, CARRIER>(g[6], g[8], w2, wd2, uy - ux, Fy - Fx, k1, om, su, a2, rho3, fb, f3, f9);
 }
 
 // ---------------------------------------------------------------------------
@@ -441,14 +492,40 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         R ux, uy;
-        collide<R, FORCH>(g[k], a[k], e[k], b[k], ph, ux, uy);
+        collide<R, FORCH, !Store<T>::kSmall>(g[k], a[k], e[k], b[k], ph, ux, uy);
         if (REDUCE && active) {
             sx += double(ux);
             sy += double(uy);
         }
     }
     float gm = 0.0f;
-    if (active) {
+    bool stored = false;
+    if constexpr (Store<T>::kSmall && VEC == 4) {
+        if (active && ph.sr) {
+            // 16-bit storage, 4 nodes: two hardware stochastic-rounding
+            // conversions per population; the random words come from one
+            // hash per thread, stepped by a multiply-add and xor-folded
+            uint32_t x = mix32(uint32_t(n0) ^ ph.step_key);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                float v[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[k] = Store<T>::kScaled ? g[k][i] * ph.scale : g[k][i];
+                if (REDUCE)
+                    gm = fmaxf(gm, fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3]))));
+                x = x * 0x2C1B3C6Du + 0x297A2D39u;
+                const uint32_t r0 = x ^ (x >> 15);
+                x = x * 0x2C1B3C6Du + 0x297A2D39u;
+                const uint32_t r1 = x ^ (x >> 15);
+                uint2 u;
+                u.x = Store<T>::pack_sr(v[0], v[1], r0);
+                u.y = Store<T>::pack_sr(v[2], v[3], r1);
+                __stcs(reinterpret_cast<uint2 *>(dst + (long long)i * geo.plane + n0), u);
+            }
+            stored = true;
+        }
+    }
+    if (active && !stored) {
         uint32_t hk[VEC];
         if constexpr (Store<T>::kSmall) {
 #pragma unroll
@@ -461,7 +538,9 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
             for (int k = 0; k < VEC; ++k) {
                 if constexpr (Store<T>::kSmall) {
                     if (ph.sr) {
-                        uint32_t r = mix32(hk[k] + uint32_t(i >> 1) * 0x9E3779B9u);
+                        // one multiply-xorshift per word on top of the node's full hash
+                        uint32_t r = (hk[k] ^ (uint32_t(i >> 1) * 0x9E3779B9u)) * 0x2C1B3C6Du;
+                        r ^= r >> 15;
                         v[k] = Store<T>::st_sr(g[k][i], ph.scale, (i & 1) ? (r >> 16) : r);
                     } else {
                         v[k] = Store<T>::st(g[k][i], ph.scale);
