@@ -71,6 +71,10 @@ def args_():
                    help="CPU-oracle sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-ttp", action="store_true",
+                   help="skip the time-to-permeability comparison")
+    p.add_argument("--ttp-n", type=int, default=1024,
+                   help="lattice side of the time-to-permeability runs")
     return p.parse_args()
 
 
@@ -255,6 +259,75 @@ def cpu_desc():
     return model
 
 
+# -- time to permeability ----------------------------------------------------
+
+TTP_CRITERION = 1e-3
+TTP_CHECK = 1000
+TTP_REF_CHECK = 10000
+TTP_REF_TOL = 1e-6
+TTP_REF_MAX = 3_000_000
+
+
+def time_to_permeability(a, variants=("f32", "f16", "bf16")):
+    """Wall time until K_app is within 1e-3 of the converged K_ref, per storage
+    format, on an n x n medium of the same recipe (seed = --seed).
+
+    K_ref: FP32 run until the mean velocity changes by less than 1e-6 per
+    10000 steps; the slowest pressure modes relax over ~1e5 steps, so that
+    leaves ~1e-5 of K_app, well inside the 1e-3 criterion.  Each variant runs
+    from rest in chunks of 1000 steps, reading K_app back after each chunk;
+    the time covers every kernel and read-back until the criterion holds."""
+    import torch
+
+    import media
+    import paper_1601_00704_gb300 as pkg
+    n = a.ttp_n
+    eps, K, _ = media.two_phase_medium(n, n, om_fraction=a.om_fraction,
+                                       corr_len=a.corr_len, seed=a.seed)
+    stream = torch.cuda.Stream()
+    ref = pkg.Solver(n, n, tau=TAU, storage="f32", stream=stream)
+    ref.set_medium(eps, K)
+    ref.set_force(G)
+    t0 = time.perf_counter()
+    ref_steps, conv = ref.step(TTP_REF_MAX, tol=TTP_REF_TOL, check_every=TTP_REF_CHECK)
+    k_ref = ref.permeability()
+    ref_s = time.perf_counter() - t0
+    ref.close()
+    runs = {}
+    for v in variants:
+        s = pkg.Solver(n, n, tau=TAU, storage=v, stream=stream)
+        s.set_medium(eps, K)
+        s.set_force(G)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps, k = 0, float("nan")
+        while steps < ref_steps:
+            s.step(TTP_CHECK)
+            steps += TTP_CHECK
+            k = s.permeability()
+            if abs(k / k_ref - 1) <= TTP_CRITERION:
+                break
+        e1.record(stream)
+        e1.synchronize()
+        runs[v] = {"seconds": e0.elapsed_time(e1) * 1e-3, "steps": steps, "k_app": k,
+                   "rel_err": k / k_ref - 1,
+                   "met": abs(k / k_ref - 1) <= TTP_CRITERION}
+        s.close()
+    base = runs.get("f32", {}).get("seconds")
+    return {
+        "workload": f"{n}x{n} two-phase medium, same recipe as config (seed {a.seed})",
+        "criterion": f"|K_app/K_ref - 1| <= {TTP_CRITERION:g}, checked every {TTP_CHECK} steps",
+        "k_ref": k_ref,
+        "k_ref_from": f"FP32 run to relative change < {TTP_REF_TOL:g} per {TTP_REF_CHECK} steps "
+                      f"({ref_steps} steps, converged={conv}, {ref_s:.1f} s)",
+        "runs": runs,
+        "speedup_vs_f32": {v: base / r["seconds"] for v, r in runs.items()
+                           if base and r["met"] and v != "f32"},
+    }
+
+
 # -- arms ---------------------------------------------------------------------
 
 def run_reference(a, world, rank):
@@ -373,6 +446,9 @@ def run_ours(a, world, rank, local):
                "sample": f"{n} time steps of the full {a.nx}x{a.ny} lattice ({dt:.1f} s), "
                          f"FP64 oracle, OpenMP over rows on {cpu_desc()}"}
     s.close()
+    ttp = None
+    if rank == 0 and not a.no_ttp:
+        ttp = time_to_permeability(a)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -383,6 +459,7 @@ def run_ours(a, world, rank, local):
             "config": workload(a),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": l1 - l0, "k_app": kapp,
+            "time_to_permeability": ttp,
         }
         print(json.dumps(line), flush=True)
     return 0
