@@ -200,6 +200,105 @@ glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst,
 /* Release all device memory of the handle.  NULL-safe. */
 void glbm_destroy(glbm_t h);
 
+/* ===========================================================================
+ * Batched media: many lattices of uneven size advanced together.
+ *
+ * All media share tau, the storage format (GLBM_F32 or GLBM_BF16DEV), the
+ * boundary flags and the body force; each has its own eps and K.  Every time
+ * step is ONE kernel launch over the row tiles of all media that have not
+ * converged; chunks of check_every steps are captured into CUDA graphs and
+ * replayed.  Per medium the arithmetic is exactly that of glbm_step on a
+ * lone lattice (same kernel body), so each medium's distributions match a
+ * single-lattice run bit for bit.  The model is the paper's Forchheimer-free
+ * one (Eq. 28).  Batches enqueue on their own stream when `stream` is NULL
+ * (graph capture needs a non-legacy stream).  The handle owns its memory.
+ * ======================================================================== */
+typedef struct glbm_batch *glbm_batch_t;
+
+/* count media with sizes nx[m] x ny[m] (nx[m] a multiple of 4, ny[m] >= 2).
+ * Errors: EINVAL (sizes, storage other than F32/BF16DEV), ENOMEM, ECUDA;
+ * the message is in glbm_batch_last_error(NULL). */
+glbm_status glbm_batch_create(int count, const int *nx, const int *ny,
+                              double tau, glbm_storage storage, unsigned flags,
+                              void *stream, glbm_batch_t *out);
+
+/* eps and K of medium `index`, [ny][nx] FP64 as in glbm_set_medium; packs
+ * its coefficients and puts it at rest. */
+glbm_status glbm_batch_set_medium(glbm_batch_t b, int index, const double *eps,
+                                  const double *K, int device_ptrs);
+
+/* Body force G for every medium; clears the convergence histories. */
+glbm_status glbm_batch_set_force(glbm_batch_t b, double gx, double gy);
+
+/* Every medium back to rest (f = f_eq(1, 0)), step counts and convergence
+ * histories cleared, all media active again. */
+glbm_status glbm_batch_reset(glbm_batch_t b);
+
+/* Block schedule: threads per block (64, 128 or 256) and tile order (0 =
+ * media in index order, 1 = largest media first, 2 = largest and smallest
+ * media alternating). */
+glbm_status glbm_batch_set_schedule(glbm_batch_t b, int threads, int order);
+
+/* Time every schedule for 2 x trial_steps steps on this batch, keep the
+ * fastest (returned in threads/order, either may be NULL) and reset the batch
+ * (the trials advance it).  Requires every medium set. */
+glbm_status glbm_batch_autotune(glbm_batch_t b, int trial_steps, int *threads,
+                                int *order);
+
+/* Advance at most n steps in chunks of check_every.  With tol > 0 each
+ * medium's mean u_x is tested at every chunk end as in glbm_step, and a
+ * medium whose relative change is <= tol leaves the batch (its state is
+ * kept); the call returns early when none is left.  steps_done and
+ * active_left (media still running) may be NULL.  ENAN names the medium. */
+glbm_status glbm_batch_step(glbm_batch_t b, long long n, double tol,
+                            int check_every, long long *steps_done,
+                            int *active_left);
+
+/* Per medium: Darcy permeability nu*Ux/Gx (kxx[count]), mean velocity
+ * (mean_u[2*count], Ux Uy pairs), steps run (steps[count]) and whether it
+ * converged (converged[count]); any pointer may be NULL. */
+glbm_status glbm_batch_results(glbm_batch_t b, double *kxx, double *mean_u,
+                               long long *steps, int *converged);
+
+/* Absolute distributions of medium `index`, [9][ny][nx] FP64 (as
+ * glbm_get_distributions). */
+glbm_status glbm_batch_get_distributions(glbm_batch_t b, int index, double *f,
+                                         int device_ptrs);
+
+/* Current schedule, kernels launched so far and total node count. */
+glbm_status glbm_batch_info(glbm_batch_t b, int *threads, int *order,
+                            long long *launches, long long *nodes);
+
+void glbm_batch_destroy(glbm_batch_t b);
+const char *glbm_batch_last_error(glbm_batch_t b);
+
+/* ===========================================================================
+ * Per-node apparent permeability from the DGM + GMS model (Sec. 2.1): Eq. 18
+ * for inorganic nodes (organic[i] = 0) and Eq. 19 for organic nodes, with
+ * K0 and K_c from Eq. 4 (pore diameter d = 2 r[i]), D_K from Eq. 3 and the
+ * ideal-gas density rho_g = P M / (R T).  SI inputs: r (m, per node), eps
+ * (per node, in (0, 1)), P (Pa), T (K), M (kg/mol), eta (Pa s), tort
+ * (tortuosity), qsat (mol/m^3), b (1/Pa), Ds (m^2/s), dx (lattice spacing,
+ * m).  K[i] receives K_app / dx^2 (lattice units, ready for set_medium).
+ * n values each; device_ptrs as elsewhere; work is enqueued on `stream`
+ * (NULL = legacy default) and the call returns when K is written.  EINVAL
+ * (message in glbm_last_error(NULL)) for a non-positive radius or bad
+ * scalars.
+ * ======================================================================== */
+glbm_status glbm_kapp_field(const double *r, const unsigned char *organic,
+                            const double *eps, long long n, double P, double T,
+                            double M, double eta, double tort, double qsat,
+                            double b, double Ds, double dx, double *K,
+                            int device_ptrs, void *stream);
+
+/* Eq. 38: saturation concentration q_sat,k (mol per m^3 of kerogen) from a
+ * Langmuir volume q_sat,b (m^3 of methane per kg of bulk shale):
+ * q_sat,b rho_b / ((1 - eps) TOC) * rho_CH4 / M_CH4.  Host arithmetic only;
+ * returns NaN for a non-positive (1 - eps) TOC or M_CH4. */
+double glbm_qsat_from_langmuir_volume(double qsat_b, double rho_b, double eps,
+                                      double toc, double rho_ch4,
+                                      double M_ch4);
+
 /* Message of the last failure on this handle (h = NULL: the last failure of
  * glbm_create or glbm_step_reduce_noalloc on this host thread).  Never NULL. */
 const char *glbm_last_error(glbm_t h);

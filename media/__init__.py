@@ -36,6 +36,7 @@ __all__ = [
     "layered_medium",
     "random_medium",
     "random_state",
+    "shale_batch",
 ]
 
 
@@ -143,3 +144,36 @@ def random_state(nx: int, ny: int, seed: int, *, amp: float = 1e-3,
     ux = u_amp * rng.standard_normal((ny, nx))
     uy = u_amp * rng.standard_normal((ny, nx))
     return rho, ux, uy
+
+
+def shale_batch(count: int = 512, *, seed: int = 0, sides=tuple(range(64, 1025, 64)),
+                om_fraction: float = 0.2, corr_len: float = 8.0,
+                r_median=(20e-9, 5e-9), sigma_ln: float = 0.5,
+                eps_phase=(0.02, 0.04), pressure=(0.5e6, 30e6),
+                langmuir_pressure=(2e6, 10e6), langmuir_volume=(0.002, 0.01)):
+    """Inputs of a batched sweep over shale media (one dict per medium).
+
+    Per medium: a square side drawn uniformly from ``sides``; an OM/IOM map
+    grown as in ``two_phase_map``; per-node pore radius lognormal around the
+    phase median (IOM first, OM second) with log-standard deviation
+    ``sigma_ln``; per-phase porosity; a pressure uniform in ``pressure`` (Pa);
+    a Langmuir pressure P_L uniform in ``langmuir_pressure`` (b = 1/P_L) and a
+    Langmuir volume V_L uniform in ``langmuir_volume`` (m^3/kg).  Everything
+    comes from one PCG64(seed) stream in a fixed order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(sides))
+        om = two_phase_map(n, n, om_fraction, corr_len, rng)
+        z = rng.standard_normal((n, n))
+        med = np.where(om, r_median[1], r_median[0])
+        r = med * np.exp(sigma_ln * z)
+        eps = np.where(om, eps_phase[1], eps_phase[0]).astype(np.float64)
+        out.append({
+            "n": n, "organic": om, "r": r, "eps": eps,
+            "P": float(rng.uniform(*pressure)),
+            "P_L": float(rng.uniform(*langmuir_pressure)),
+            "V_L": float(rng.uniform(*langmuir_volume)),
+            "toc": float(om.mean()),
+        })
+    return out

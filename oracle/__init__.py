@@ -38,6 +38,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "glbm_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "dgm_gms.c"), os.path.join(_HERE, "em_gmm.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LOCK = threading.Lock()
 _LIBS: dict[bool, C.CDLL] = {}
@@ -56,12 +57,13 @@ def build(force: bool = False) -> None:
     os.makedirs(_BUILD, exist_ok=True)
     for omp in (False, True):
         out = _lib_path(omp)
+        srcs = [p for p in _SRCS if os.path.exists(p)]
         if (not force and os.path.exists(out)
-                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(out) >= max(os.path.getmtime(p) for p in srcs)):
             continue
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+               "-shared", "-fPIC", *srcs, "-o", tmp, "-lm"]
         if omp:
             cmd.insert(1, "-fopenmp")
         subprocess.run(cmd, check=True)
@@ -94,6 +96,14 @@ def _lib(omp: bool = False) -> C.CDLL:
             lib.orc_permeability.argtypes = [_D, _D, _D]
             lib.orc_threads.restype = C.c_int
             lib.orc_threads.argtypes = [C.c_int]
+            lib.orc_dgm_kc_k0.argtypes = [_D, _D, _D, _PD, _PD]
+            lib.orc_knudsen_diffusivity.restype = _D
+            lib.orc_knudsen_diffusivity.argtypes = [_D, _D, _D]
+            lib.orc_kapp.restype = _D
+            lib.orc_kapp.argtypes = [_D] * 7 + [C.c_int] + [_D] * 3
+            lib.orc_qsat_from_langmuir_volume.restype = _D
+            lib.orc_qsat_from_langmuir_volume.argtypes = [_D] * 6
+            lib.orc_kapp_field.argtypes = [_PD, C.POINTER(C.c_ubyte), _PD, C.c_long] + [_D] * 9 + [_PD]
             _LIBS[omp] = lib
         return _LIBS[omp]
 
@@ -165,6 +175,47 @@ def init_equilibrium(eps, rho=None, ux=None, uy=None):
     _lib().orc_init_equilibrium(nx, ny, _ptr(eps), _ptr(_f64(rho)),
                                 _ptr(_f64(ux)), _ptr(_f64(uy)), _ptr(f))
     return f
+
+
+# -- DGM/GMS apparent permeability (Sec. 2.1) --------------------------------
+
+METHANE_M = 0.01604  # kg/mol
+
+
+def dgm_kc_k0(r, eps, tort):
+    """Eq. 4 -> (K_c, K0) for pore radius r."""
+    a, b = _D(), _D()
+    _lib().orc_dgm_kc_k0(r, eps, tort, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def knudsen_diffusivity(Kc, T, M=METHANE_M):
+    """Eq. 3."""
+    return _lib().orc_knudsen_diffusivity(Kc, T, M)
+
+
+def kapp(r, P, T, eta, eps, tort, organic, qsat=0.0, b=0.0, Ds=0.0, M=METHANE_M):
+    """Eq. 18 (organic=False) or Eq. 19 (organic=True), SI units, m^2."""
+    return _lib().orc_kapp(r, P, T, M, eta, eps, tort, int(bool(organic)),
+                           qsat, b, Ds)
+
+
+def qsat_from_langmuir_volume(qsat_b, rho_b, eps, toc, rho_ch4, M_ch4=METHANE_M):
+    """Eq. 38: Langmuir volume (m^3/kg) -> q_sat (mol/m^3 of kerogen)."""
+    return _lib().orc_qsat_from_langmuir_volume(qsat_b, rho_b, eps, toc,
+                                                rho_ch4, M_ch4)
+
+
+def kapp_field(r, organic, eps, P, T, eta, tort, qsat, b, Ds, dx, M=METHANE_M):
+    """Per-node K_app / dx^2 (lattice units) for arrays r, organic, eps."""
+    r = _f64(r)
+    org = np.ascontiguousarray(organic, dtype=np.uint8)
+    e = _f64(eps)
+    K = np.empty_like(r)
+    _lib().orc_kapp_field(_ptr(r), org.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                          _ptr(e), r.size, P, T, M, eta, tort, qsat, b, Ds, dx,
+                          _ptr(K))
+    return K
 
 
 class Oracle:

@@ -19,8 +19,8 @@ import numpy as np
 
 from .build import LIB as LIB_PATH
 
-__all__ = ["Solver", "GLBMError", "load", "F32", "F64", "F16DEV", "BF16DEV",
-           "WALLS_Y", "PERIODIC_Y", "NEAREST16", "STORAGE"]
+__all__ = ["Solver", "Batch", "kapp_field", "GLBMError", "load", "F32", "F64",
+           "F16DEV", "BF16DEV", "WALLS_Y", "PERIODIC_Y", "NEAREST16", "STORAGE"]
 
 F32, F64, F16DEV, BF16DEV = 0, 1, 2, 3
 STORAGE = {"f32": F32, "f64": F64, "f16": F16DEV, "bf16": BF16DEV}
@@ -34,7 +34,12 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_init_equilibrium", "glbm_step", "glbm_mean_velocity",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
-           "glbm_step_reduce_noalloc"]
+           "glbm_step_reduce_noalloc",
+           "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
+           "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
+           "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
+           "glbm_batch_info", "glbm_batch_destroy", "glbm_batch_last_error",
+           "glbm_kapp_field", "glbm_qsat_from_langmuir_volume"]
 
 
 class GLBMError(RuntimeError):
@@ -75,6 +80,20 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_last_error": ([h], C.c_char_p),
         "glbm_step_reduce_noalloc": ([_VP, _VP, _VP, _VP, _VP, i, i, ll, d, d, d,
                                       C.c_uint, _VP, _VP], i),
+        "glbm_batch_create": ([i, _VP, _VP, d, i, C.c_uint, _VP, C.POINTER(_VP)], i),
+        "glbm_batch_set_medium": ([h, i, _VP, _VP, i], i),
+        "glbm_batch_set_force": ([h, d, d], i),
+        "glbm_batch_reset": ([h], i),
+        "glbm_batch_set_schedule": ([h, i, i], i),
+        "glbm_batch_autotune": ([h, i, C.POINTER(i), C.POINTER(i)], i),
+        "glbm_batch_step": ([h, ll, d, i, C.POINTER(ll), C.POINTER(i)], i),
+        "glbm_batch_results": ([h, _VP, _VP, _VP, _VP], i),
+        "glbm_batch_get_distributions": ([h, i, _VP, i], i),
+        "glbm_batch_info": ([h, C.POINTER(i), C.POINTER(i), C.POINTER(ll), C.POINTER(ll)], i),
+        "glbm_batch_destroy": ([h], None),
+        "glbm_batch_last_error": ([h], C.c_char_p),
+        "glbm_kapp_field": ([_VP, _VP, _VP, ll, d, d, d, d, d, d, d, d, d, _VP, i, _VP], i),
+        "glbm_qsat_from_langmuir_volume": ([d] * 6, d),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -238,3 +257,118 @@ class Solver:
         s, l = C.c_longlong(), C.c_longlong()
         self._check(self._lib.glbm_counters(self._h, C.byref(s), C.byref(l)))
         return s.value, l.value
+
+
+class Batch:
+    """Many media of uneven size advanced together (a ``glbm_batch_t``).
+
+    ``shapes`` is a list of (ny, nx) with nx a multiple of 4; ``storage`` is
+    'f32' or 'bf16'.  Each medium matches a lone ``Solver`` bit for bit."""
+
+    def __init__(self, shapes, tau=1.0, storage="f32", walls=True, stream=None):
+        self._lib = load()
+        self._h = _VP()
+        self.shapes = [(int(ny), int(nx)) for ny, nx in shapes]
+        self.tau = float(tau)
+        n = len(self.shapes)
+        nxs = (C.c_int * n)(*[nx for _, nx in self.shapes])
+        nys = (C.c_int * n)(*[ny for ny, _ in self.shapes])
+        st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        sv = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
+        rc = self._lib.glbm_batch_create(n, nxs, nys, self.tau, st,
+                                         WALLS_Y if walls else PERIODIC_Y,
+                                         _VP(sv) if sv else None, C.byref(self._h))
+        if rc != 0:
+            raise GLBMError(rc, self._lib.glbm_batch_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc != 0:
+            raise GLBMError(rc, self._lib.glbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.glbm_batch_destroy(self._h)
+            self._h = _VP()
+
+    __del__ = close
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def set_medium(self, index, eps, K):
+        shape = self.shapes[index]
+        e, k = _Arg(eps, shape), _Arg(K, shape)
+        if e.device != k.device:
+            raise ValueError("eps and K must both be host or both device arrays")
+        self._check(self._lib.glbm_batch_set_medium(self._h, int(index), e.ptr, k.ptr,
+                                                    int(e.device)))
+
+    def set_force(self, gx, gy=0.0):
+        self._check(self._lib.glbm_batch_set_force(self._h, float(gx), float(gy)))
+
+    def reset(self):
+        self._check(self._lib.glbm_batch_reset(self._h))
+
+    def set_schedule(self, threads, order):
+        self._check(self._lib.glbm_batch_set_schedule(self._h, int(threads), int(order)))
+
+    def autotune(self, trial_steps=20):
+        t, o = C.c_int(), C.c_int()
+        self._check(self._lib.glbm_batch_autotune(self._h, int(trial_steps),
+                                                  C.byref(t), C.byref(o)))
+        return t.value, o.value
+
+    def step(self, n, tol=0.0, check_every=100):
+        done, left = C.c_longlong(), C.c_int()
+        self._check(self._lib.glbm_batch_step(self._h, int(n), float(tol), int(check_every),
+                                              C.byref(done), C.byref(left)))
+        return done.value, left.value
+
+    def results(self):
+        """-> dict of per-medium arrays: kxx, mean_u (count x 2), steps, converged."""
+        n = len(self.shapes)
+        k = np.empty(n)
+        u = np.empty((n, 2))
+        st = np.empty(n, dtype=np.int64)
+        cv = np.empty(n, dtype=np.int32)
+        self._check(self._lib.glbm_batch_results(self._h, k.ctypes.data, u.ctypes.data,
+                                                 st.ctypes.data, cv.ctypes.data))
+        return {"kxx": k, "mean_u": u, "steps": st, "converged": cv.astype(bool)}
+
+    def distributions(self, index):
+        shape = (9,) + self.shapes[index]
+        out = np.empty(shape)
+        self._check(self._lib.glbm_batch_get_distributions(self._h, int(index),
+                                                           out.ctypes.data, 0))
+        return out
+
+    def info(self):
+        t, o, l, nn = C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()
+        self._check(self._lib.glbm_batch_info(self._h, C.byref(t), C.byref(o), C.byref(l),
+                                              C.byref(nn)))
+        return {"threads": t.value, "order": o.value, "launches": l.value, "nodes": nn.value}
+
+
+def qsat_from_langmuir_volume(qsat_b, rho_b, eps, toc, rho_ch4, M_ch4=0.01604):
+    """Eq. 38 (via the C ABI): Langmuir volume (m^3/kg) -> q_sat (mol/m^3)."""
+    return load().glbm_qsat_from_langmuir_volume(float(qsat_b), float(rho_b), float(eps),
+                                                 float(toc), float(rho_ch4), float(M_ch4))
+
+
+def kapp_field(r, organic, eps, P, T, eta, tort, qsat, b, Ds, dx, M=0.01604):
+    """Per-node DGM/GMS apparent permeability in lattice units (Eqs. 18-19):
+    NumPy inputs of equal shape -> K_app / dx^2 as float64, same shape."""
+    lib = load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    org = np.ascontiguousarray(organic, dtype=np.uint8)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    if not (r.shape == org.shape == e.shape):
+        raise ValueError("r, organic and eps must have one shape")
+    K = np.empty_like(r)
+    rc = lib.glbm_kapp_field(r.ctypes.data, org.ctypes.data, e.ctypes.data, r.size,
+                             float(P), float(T), float(M), float(eta), float(tort),
+                             float(qsat), float(b), float(Ds), float(dx),
+                             K.ctypes.data, 0, None)
+    if rc != 0:
+        raise GLBMError(rc, lib.glbm_last_error(None).decode())
+    return K

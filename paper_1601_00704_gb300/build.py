@@ -8,7 +8,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "glbm.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu")]
+HDR = [os.path.join(HERE, "csrc", "glbm_kernels.cuh")]
+OBJ = os.path.join(HERE, "csrc", "_obj")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libglbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -25,7 +27,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = SRC + [os.path.join(INCLUDE, "glbm.h"), __file__]
+    deps = SRC + HDR + [os.path.join(INCLUDE, "glbm.h"), __file__]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -34,17 +36,37 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if not force and not _stale():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared",
-           "-Xcompiler", "-fPIC", "-I", INCLUDE, *SRC, "-o", tmp]
+    os.makedirs(OBJ, exist_ok=True)
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
+        flags.insert(0, "-Xptxas=-v")
     if extra:
-        cmd[1:1] = extra
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        flags = list(extra) + flags
+    procs, objs = [], []
+    for src in SRC:
+        obj = os.path.join(OBJ, os.path.basename(src) + f".{os.getpid()}.o")
+        objs.append(obj)
+        procs.append((src, subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj],
+                                            stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                            text=True)))
+    log = ""
+    failed = False
+    for src, p in procs:
+        out, _ = p.communicate()
+        log += out
+        failed = failed or p.returncode != 0
+    if not failed:
+        r = subprocess.run([nvcc(), *ARCH, "-shared", *objs, "-o", tmp],
+                           capture_output=True, text=True)
+        log += r.stdout + r.stderr
+        failed = r.returncode != 0
+    for o in objs:
+        if os.path.exists(o):
+            os.remove(o)
+    if failed:
+        raise RuntimeError("nvcc failed:\n" + log)
     if verbose:
-        print(r.stdout + r.stderr)
+        print(log)
     os.replace(tmp, LIB)
     return LIB
 

@@ -1,0 +1,142 @@
+"""Batched media (one launch per step for many lattices) and the DGM/GMS
+per-node permeability builder, against single-lattice runs and the oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+import media
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(48, 64), (32, 128), (80, 36), (17, 516), (64, 64)]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1601_00704_gb300 import build
+    build.build()
+    import paper_1601_00704_gb300 as p
+    return p
+
+
+def media_for(shapes, seed=0):
+    out = []
+    for i, (ny, nx) in enumerate(shapes):
+        eps, K = media.random_medium(nx, ny, seed=seed + i, k_range=(1e-3, 1e0))
+        out.append((eps, K))
+    return out
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("walls", [True, False])
+def test_batch_matches_single_bitwise(pkg, storage, walls):
+    """Each medium of a batch evolves exactly as it would alone (same kernel
+    body, same stochastic-rounding keys), across chunks replayed from a
+    captured graph."""
+    md = media_for(SHAPES)
+    b = pkg.Batch(SHAPES, tau=0.8, storage=storage, walls=walls)
+    for i, (eps, K) in enumerate(md):
+        b.set_medium(i, eps, K)
+    b.set_force(2e-5, -5e-6)
+    done, left = b.step(37, check_every=10)
+    assert done == 37 and left == len(SHAPES)
+    res = b.results()
+    for i, ((ny, nx), (eps, K)) in enumerate(zip(SHAPES, md)):
+        s = pkg.Solver(nx, ny, tau=0.8, storage=storage, walls=walls)
+        s.set_medium(eps, K)
+        s.set_force(2e-5, -5e-6)
+        s.step(37)
+        assert np.array_equal(b.distributions(i), s.distributions()), i
+        assert res["kxx"][i] == pytest.approx(s.permeability(), rel=1e-13)
+        assert res["steps"][i] == 37
+
+
+def test_schedule_does_not_change_results(pkg):
+    md = media_for(SHAPES, seed=5)
+    outs = []
+    for threads, order in ((64, 0), (256, 2), (128, 1)):
+        b = pkg.Batch(SHAPES, storage="bf16")
+        for i, (eps, K) in enumerate(md):
+            b.set_medium(i, eps, K)
+        b.set_force(1e-5)
+        b.set_schedule(threads, order)
+        b.step(25, check_every=7)
+        outs.append([b.distributions(i) for i in range(len(SHAPES))])
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
+
+
+def test_autotune_picks_a_schedule_and_resets(pkg):
+    md = media_for(SHAPES, seed=9)
+    b = pkg.Batch(SHAPES)
+    for i, (eps, K) in enumerate(md):
+        b.set_medium(i, eps, K)
+    b.set_force(1e-5)
+    t, o = b.autotune(trial_steps=5)
+    assert t in (64, 128, 256) and o in (0, 1, 2)
+    assert b.info()["threads"] == t
+    b.step(12, check_every=12)
+    fresh = pkg.Batch(SHAPES)
+    for i, (eps, K) in enumerate(md):
+        fresh.set_medium(i, eps, K)
+    fresh.set_force(1e-5)
+    fresh.step(12, check_every=12)
+    for i in range(len(SHAPES)):
+        assert np.array_equal(b.distributions(i), fresh.distributions(i))
+
+
+def test_converged_media_leave_the_batch(pkg):
+    """Small media converge first, leave the tile table, and keep their state
+    while the others run on; results match each medium run alone to its own
+    convergence."""
+    # clear channels (eps = 1, K = inf): viscous relaxation time ~ H^2 / nu
+    shapes = [(8, 8), (16, 16), (48, 64)]
+    md = [media.uniform_medium(nx, ny, 1.0, math.inf) for ny, nx in shapes]
+    b = pkg.Batch(shapes)
+    for i, (eps, K) in enumerate(md):
+        b.set_medium(i, eps, K)
+    b.set_force(1e-5)
+    done, left = b.step(200000, tol=1e-9, check_every=100)
+    res = b.results()
+    assert left == 0 and res["converged"].all()
+    assert len(set(res["steps"].tolist())) > 1
+    for i, ((ny, nx), (eps, K)) in enumerate(zip(shapes, md)):
+        s = pkg.Solver(nx, ny)
+        s.set_medium(eps, K)
+        s.set_force(1e-5)
+        n, conv = s.step(200000, tol=1e-9, check_every=100)
+        assert conv and n == res["steps"][i]
+        assert np.array_equal(b.distributions(i), s.distributions())
+
+
+def test_batch_errors(pkg):
+    with pytest.raises(pkg.GLBMError):
+        pkg.Batch([(8, 6)])  # nx not a multiple of 4
+    with pytest.raises(pkg.GLBMError):
+        pkg.Batch([(8, 8)], storage="f16")
+    b = pkg.Batch([(8, 8), (8, 12)])
+    with pytest.raises(pkg.GLBMError) as e:
+        b.step(1)
+    assert e.value.name == "GLBM_ESTATE"
+
+
+def test_kapp_field_matches_oracle(pkg, orc):
+    """glbm_kapp_field (simplified algebra on the GPU) equals the oracle's
+    literal Eq. 18/19 evaluation node by node."""
+    rng = np.random.default_rng(3)
+    n = 5000
+    r = rng.lognormal(math.log(8e-9), 0.6, n)
+    org = rng.random(n) < 0.3
+    eps = np.where(org, 0.04, 0.02)
+    for P in (0.5e6, 5e6, 30e6):
+        args = (P, 350.0, 18.231e-6, 2.0, 3000.0, 1 / 4e6, 1e-8, 7.8125e-9)
+        got = pkg.kapp_field(r, org, eps, *args)
+        want = orc.kapp_field(r, org, eps, *args)
+        np.testing.assert_allclose(got, want, rtol=1e-13)
+    assert pkg.qsat_from_langmuir_volume(0.005, 1.65e3, 0.04, 0.2, 0.717) == pytest.approx(
+        orc.qsat_from_langmuir_volume(0.005, 1.65e3, 0.04, 0.2, 0.717), rel=1e-15)
+    with pytest.raises(pkg.GLBMError):
+        pkg.kapp_field(np.zeros(4), np.zeros(4, bool), np.full(4, 0.02), *args)
