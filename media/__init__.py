@@ -64,10 +64,14 @@ def two_phase_map(nx: int, ny: int, om_fraction: float, corr_len: float,
     field = gaussian_random_field(nx, ny, corr_len, rng).ravel()
     n = field.size
     n_om = int(round(om_fraction * n))
-    # stable sort of -field: equal values keep ascending linear index
-    order = np.argsort(-field, kind="stable")
     mask = np.zeros(n, dtype=bool)
-    mask[order[:n_om]] = True
+    if n_om > 0:
+        # the n_om-th largest value, then every larger value plus the lowest
+        # linear indices among values equal to it (same set as a stable sort)
+        thr = np.partition(field, n - n_om)[n - n_om]
+        mask = field > thr
+        ties = np.flatnonzero(field == thr)
+        mask[ties[:n_om - int(mask.sum())]] = True
     return mask.reshape(ny, nx)
 
 

@@ -38,3 +38,34 @@ def test_layered_and_uniform():
     assert np.all(K[:, :4] == 1.0) and np.all(K[:, 4:] == 2.0)
     e, k = media.uniform_medium(3, 2, 0.5, np.inf)
     assert np.all(np.isinf(k)) and np.all(e == 0.5)
+
+
+def test_phase_threshold_equals_stable_sort_definition():
+    """OM = the round(phi*N) largest field values, ties to the lowest index."""
+    for seed in range(3):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        om = media.two_phase_map(96, 80, 0.3, 6, rng)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        f = media.gaussian_random_field(96, 80, 6, rng).ravel()
+        order = np.argsort(-f, kind="stable")
+        want = np.zeros(f.size, bool)
+        want[order[:round(0.3 * f.size)]] = True
+        assert np.array_equal(om.ravel(), want)
+    f = np.array([1.0, 2.0, 2.0, 2.0, 0.5])  # exact ties: lowest index first
+    thr_mask = np.zeros(5, bool)
+    thr = np.partition(f, 5 - 2)[5 - 2]
+    thr_mask = f > thr
+    ties = np.flatnonzero(f == thr)
+    thr_mask[ties[:2 - int(thr_mask.sum())]] = True
+    assert thr_mask.tolist() == [False, True, True, False, False]
+
+
+def test_shale_batch_recipe():
+    b = media.shale_batch(6, seed=1)
+    assert len(b) == 6
+    for m in b:
+        assert m["n"] % 64 == 0 and 64 <= m["n"] <= 1024
+        assert m["r"].shape == (m["n"], m["n"]) and (m["r"] > 0).all()
+        assert 0.5e6 <= m["P"] <= 30e6 and 2e6 <= m["P_L"] <= 10e6
+        assert 0.002 <= m["V_L"] <= 0.01
+        assert abs(np.median(m["r"][m["organic"]]) / 5e-9 - 1) < 0.2
