@@ -265,6 +265,11 @@ glbm_status glbm_batch_results(glbm_batch_t b, double *kxx, double *mean_u,
 glbm_status glbm_batch_get_distributions(glbm_batch_t b, int index, double *f,
                                          int device_ptrs);
 
+/* Density (Eq. 32) and Eq. 34 velocity of medium `index` at its last step,
+ * [ny][nx] FP64 each (rho may be NULL).  ESTATE before the first step. */
+glbm_status glbm_batch_get_fields(glbm_batch_t b, int index, double *rho,
+                                  double *ux, double *uy, int device_ptrs);
+
 /* Current schedule, kernels launched so far and total node count. */
 glbm_status glbm_batch_info(glbm_batch_t b, int *threads, int *order,
                             long long *launches, long long *nodes);
@@ -302,6 +307,72 @@ double glbm_qsat_from_langmuir_volume(double qsat_b, double rho_b, double eps,
 /* Message of the last failure on this handle (h = NULL: the last failure of
  * glbm_create or glbm_step_reduce_noalloc on this host thread).  Never NULL. */
 const char *glbm_last_error(glbm_t h);
+
+/* ===========================================================================
+ * Network kernels of the learned warm start.  The paper has no surrogate:
+ * these exist so that a small U-Net, trained by this library on the solver's
+ * own converged fields, can predict the steady density deviation and
+ * velocity of a new medium, from which glbm_init_equilibrium starts the
+ * solver.  FP32, NCHW device tensors; each tensor is passed as (pointer,
+ * per-sample stride in floats), so a layer may read or write a channel slice
+ * of a larger tensor.  Convolutions use zero padding ksize/2 (ksize 1 or 3)
+ * and weights laid out [cout][cin][ksize][ksize].  All calls enqueue on
+ * `stream` and return EINVAL for bad sizes or NULL pointers, ECUDA for a
+ * failed launch.
+ * ======================================================================== */
+
+/* y = conv(x) + bias (bias may be NULL), then max(., 0) when relu != 0. */
+glbm_status glbm_nn_conv_fwd(const float *x, long long xbs, int cin, float *y,
+                             long long ybs, int cout, int n, int h, int w,
+                             int ksize, const float *wt, const float *bias,
+                             int relu, void *stream);
+
+/* dx = dL/dx of y = conv(x) given dy; wt_scratch holds cout*cin*ksize^2
+ * floats (the flipped, transposed weights). */
+glbm_status glbm_nn_conv_bwd_data(const float *dy, long long dybs, int cout,
+                                  float *dx, long long dxbs, int cin, int n,
+                                  int h, int w, int ksize, const float *wt,
+                                  float *wt_scratch, void *stream);
+
+/* dw += dL/dw and db += dL/db (db may be NULL); the caller zeroes them. */
+glbm_status glbm_nn_conv_bwd_weight(const float *x, long long xbs, int cin,
+                                    const float *dy, long long dybs, int cout,
+                                    int n, int h, int w, int ksize, float *dw,
+                                    float *db, void *stream);
+
+/* dy[i] = 0 where y[i] <= 0 (ReLU backward, in place). */
+glbm_status glbm_nn_relu_bwd(const float *y, long long ybs, float *dy,
+                             long long dybs, int c, int n, int h, int w,
+                             void *stream);
+
+/* dst[:, 0:c] = src[:, 0:c] (accumulate != 0: +=). */
+glbm_status glbm_nn_copy_channels(const float *src, long long sbs, float *dst,
+                                  long long dbs, int c, int n, int h, int w,
+                                  int accumulate, void *stream);
+
+/* 2x2 average pool of an h x w input; backward != 0: x is dy (h/2 x w/2),
+ * y receives dx (h x w), += when accumulate != 0. */
+glbm_status glbm_nn_pool2(const float *x, long long xbs, float *y,
+                          long long ybs, int c, int n, int h, int w,
+                          int backward, int accumulate, void *stream);
+
+/* Nearest 2x upsample of an h x w input; backward != 0: x is dy (2h x 2w),
+ * y receives dx (h x w). */
+glbm_status glbm_nn_upsample2(const float *x, long long xbs, float *y,
+                              long long ybs, int c, int n, int h, int w,
+                              int backward, void *stream);
+
+/* loss += sum_c channel_weight[c] * mean over (n, pixels) of
+ * (pred - target)^2 (loss: one device double); grad = dloss/dpred (may be
+ * NULL).  Contiguous NCHW tensors. */
+glbm_status glbm_nn_mse(const float *pred, const float *target,
+                        const float *channel_weight, int c, int n, int h,
+                        int w, float *grad, double *loss, void *stream);
+
+/* Adam update of count parameters (step t >= 1, bias-corrected). */
+glbm_status glbm_nn_adam(float *p, const float *g, float *m, float *v,
+                         long long count, float lr, float beta1, float beta2,
+                         float eps, int t, void *stream);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,11 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
            "glbm_batch_info", "glbm_batch_destroy", "glbm_batch_last_error",
-           "glbm_kapp_field", "glbm_qsat_from_langmuir_volume"]
+           "glbm_kapp_field", "glbm_qsat_from_langmuir_volume",
+           "glbm_batch_get_fields",
+           "glbm_nn_conv_fwd", "glbm_nn_conv_bwd_data", "glbm_nn_conv_bwd_weight",
+           "glbm_nn_relu_bwd", "glbm_nn_copy_channels", "glbm_nn_pool2",
+           "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam"]
 
 
 class GLBMError(RuntimeError):
@@ -94,6 +98,17 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_batch_last_error": ([h], C.c_char_p),
         "glbm_kapp_field": ([_VP, _VP, _VP, ll, d, d, d, d, d, d, d, d, d, _VP, i, _VP], i),
         "glbm_qsat_from_langmuir_volume": ([d] * 6, d),
+        "glbm_batch_get_fields": ([h, i, _VP, _VP, _VP, i], i),
+        "glbm_nn_conv_fwd": ([_VP, ll, i, _VP, ll, i, i, i, i, i, _VP, _VP, i, _VP], i),
+        "glbm_nn_conv_bwd_data": ([_VP, ll, i, _VP, ll, i, i, i, i, i, _VP, _VP, _VP], i),
+        "glbm_nn_conv_bwd_weight": ([_VP, ll, i, _VP, ll, i, i, i, i, i, _VP, _VP, _VP], i),
+        "glbm_nn_relu_bwd": ([_VP, ll, _VP, ll, i, i, i, i, _VP], i),
+        "glbm_nn_copy_channels": ([_VP, ll, _VP, ll, i, i, i, i, i, _VP], i),
+        "glbm_nn_pool2": ([_VP, ll, _VP, ll, i, i, i, i, i, i, _VP], i),
+        "glbm_nn_upsample2": ([_VP, ll, _VP, ll, i, i, i, i, i, _VP], i),
+        "glbm_nn_mse": ([_VP, _VP, _VP, i, i, i, i, _VP, _VP, _VP], i),
+        "glbm_nn_adam": ([_VP, _VP, _VP, _VP, ll, C.c_float, C.c_float, C.c_float,
+                          C.c_float, i, _VP], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -341,6 +356,14 @@ class Batch:
         self._check(self._lib.glbm_batch_get_distributions(self._h, int(index),
                                                            out.ctypes.data, 0))
         return out
+
+    def fields(self, index):
+        """(rho, ux, uy) of medium `index` at its last step, FP64 (ny, nx) each."""
+        shape = self.shapes[index]
+        rho, ux, uy = np.empty(shape), np.empty(shape), np.empty(shape)
+        self._check(self._lib.glbm_batch_get_fields(self._h, int(index), rho.ctypes.data,
+                                                    ux.ctypes.data, uy.ctypes.data, 0))
+        return rho, ux, uy
 
     def info(self):
         t, o, l, nn = C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong()

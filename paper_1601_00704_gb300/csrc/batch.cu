@@ -667,6 +667,59 @@ glbm_status glbm_batch_get_distributions(glbm_batch_t h, int index, double *f, i
     return GLBM_OK;
 }
 
+glbm_status glbm_batch_get_fields(glbm_batch_t h, int index, double *rho, double *ux, double *uy, int device_ptrs) {
+    if (glbm_status s = bcheck(h)) return s;
+    if (index < 0 || index >= h->count || !ux || !uy) return bfail(h, GLBM_EINVAL, "batch_get_fields: bad arguments");
+    if (!h->reduced) return bfail(h, GLBM_ESTATE, "batch_get_fields: no step has completed since the last reset");
+    const BMed &md = h->med[index];
+    const long long N = (long long)md.nx * md.ny;
+    // the last step of this medium read the other buffer
+    const int cur = h->active[index] ? h->parity : h->parity_of[index];
+    double *tmp = nullptr, *dr = rho, *dx = ux, *dy = uy;
+    if (!device_ptrs) {
+        BCU(h, cudaMalloc(&tmp, sizeof(double) * 3 * N));
+        dr = rho ? tmp : nullptr;
+        dx = tmp + N;
+        dy = tmp + 2 * N;
+    }
+    Geo geo;
+    geo.nx = md.nx;
+    geo.ny = md.ny;
+    geo.plane = md.plane;
+    geo.bpr = (md.nx + kThreads - 1) / kThreads;
+    Phys<float> ph;
+    ph.omega = float(1.0 / h->tau);
+    ph.A = float(1.0 - 0.5 / h->tau);
+    ph.gx = float(h->gx);
+    ph.gy = float(h->gy);
+    ph.scale = 1.0f;
+    ph.inv_scale = 1.0f;
+    ph.step_key = 0;
+    ph.sr = 1;
+    const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
+    const bool walls = !(h->flags & GLBM_PERIODIC_Y);
+    const float *a = h->coef[0] + md.off_c, *e = h->coef[1] + md.off_c;
+    if (h->storage == GLBM_BF16DEV) {
+        const __nv_bfloat16 *src = static_cast<const __nv_bfloat16 *>(h->buf[cur ^ 1]) + md.off_f;
+        if (walls) k_velocity<__nv_bfloat16, true, false><<<grid, kThreads, 0, h->stream>>>(src, a, e, nullptr, geo, ph, dx, dy, dr);
+        else k_velocity<__nv_bfloat16, false, false><<<grid, kThreads, 0, h->stream>>>(src, a, e, nullptr, geo, ph, dx, dy, dr);
+    } else {
+        const float *src = static_cast<const float *>(h->buf[cur ^ 1]) + md.off_f;
+        if (walls) k_velocity<float, true, false><<<grid, kThreads, 0, h->stream>>>(src, a, e, nullptr, geo, ph, dx, dy, dr);
+        else k_velocity<float, false, false><<<grid, kThreads, 0, h->stream>>>(src, a, e, nullptr, geo, ph, dx, dy, dr);
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess && !device_ptrs) {
+        if (rho) err = cudaMemcpyAsync(rho, dr, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(ux, dx, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(uy, dy, sizeof(double) * N, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    if (tmp) cudaFree(tmp);
+    if (err != cudaSuccess) return bfail(h, GLBM_ECUDA, "batch_get_fields: %s", cudaGetErrorString(err));
+    return GLBM_OK;
+}
+
 glbm_status glbm_batch_info(glbm_batch_t h, int *threads, int *order, long long *launches, long long *nodes) {
     if (!h) return GLBM_EINVAL;
     if (threads) *threads = h->threads;

@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(kThreads)
 k_velocity(const T *__restrict__ src, const typename Store<T>::R *__restrict__ alpha,
            const typename Store<T>::R *__restrict__ epsv, const typename Store<T>::R *__restrict__ betav,
            Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ ux_out,
-           double *__restrict__ uy_out) {
+           double *__restrict__ uy_out, double *__restrict__ rho_out = nullptr) {
     using R = typename Store<T>::R;
     const int y = blockIdx.x / geo.bpr;
     const int bx = blockIdx.x - y * geo.bpr;
@@ -745,6 +745,7 @@ k_velocity(const T *__restrict__ src, const typename Store<T>::R *__restrict__ a
     node_velocity<R, FORCH>(g[0], alpha[n], epsv[n], FORCH ? betav[n] : R(0), ph, drho, ux, uy);
     ux_out[n] = double(ux);
     uy_out[n] = double(uy);
+    if (rho_out) rho_out[n] = 1.0 + double(drho);
 }
 
 // Export absolute distributions f_i = g_i + w_i in FP64.

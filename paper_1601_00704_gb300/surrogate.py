@@ -1,0 +1,263 @@
+"""Learned warm start for the GLBM time loop.
+
+The slow part of a GLBM run is the relaxation of the pressure (density)
+field, which diffuses with D ~ c_s^2 K / nu; the velocity follows it within a
+few steps through the local Darcy balance.  A start from the exact steady
+velocity with a flat density therefore saves nothing, while a start from the
+steady density saves almost all of the run.  The surrogate is a U-Net that
+maps the medium (eps, log10 K, G) to the steady density deviation and
+velocity; ``glbm_init_equilibrium`` then starts the solver from
+f = f_eq(rho_pred, u_pred), and the solver still runs to the same
+convergence test, which judges the prediction.  The paper has no surrogate:
+this is the library's own addition.
+
+Every computation of the network runs in the library's CUDA kernels
+(``glbm_nn_*``): 3x3 / 1x1 convolutions (forward, backward-data,
+backward-weight), 2x2 average pooling, nearest upsampling, ReLU, weighted
+MSE and Adam.  PyTorch only provides device memory and the stream.
+
+Normalisation (all inputs/targets dimensionless, O(1)):
+  inputs   (eps - 0.05) / 0.05,  (log10 K + 2) / 2,  log10(|G|) + 6
+  targets  delta_rho / (G * RHO_SCALE),  u * nu / (K G)  (x and y)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import GLBMError, load
+
+RHO_SCALE = 30.0
+
+
+def _ptr(t, offset_floats=0):
+    return C.c_void_p(t.data_ptr() + 4 * int(offset_floats))
+
+
+class UNet:
+    """U-Net with ``levels`` resolutions (channels base * 2^l), two 3x3
+    convolutions + ReLU per level, average-pool down, nearest-up + skip
+    concatenation, and a 1x1 head.  FP32 parameters in one flat device
+    vector (layout of ``layer_specs``)."""
+
+    def __init__(self, in_ch=3, out_ch=3, base=32, levels=4, seed=0):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.in_ch, self.out_ch, self.base, self.levels = in_ch, out_ch, base, levels
+        self.ch = [base * 2 ** l for l in range(levels)]
+        self.specs = []
+        cin = in_ch
+        for l in range(levels):
+            self.specs += [(f"e{l}a", cin, self.ch[l], 3), (f"e{l}b", self.ch[l], self.ch[l], 3)]
+            cin = self.ch[l]
+        for l in range(levels - 2, -1, -1):
+            self.specs += [(f"d{l}a", self.ch[l + 1] + self.ch[l], self.ch[l], 3),
+                           (f"d{l}b", self.ch[l], self.ch[l], 3)]
+        self.specs.append(("head", self.ch[0], out_ch, 1))
+        self.offsets = {}
+        off = 0
+        for name, ci, co, k in self.specs:
+            self.offsets[name] = (off, off + co * ci * k * k)
+            off += co * ci * k * k + co
+        self.nparams = off
+        rng = np.random.default_rng(seed)
+        init = np.zeros(off, dtype=np.float32)
+        for name, ci, co, k in self.specs:
+            ow, ob = self.offsets[name]
+            init[ow:ob] = rng.normal(0.0, np.sqrt(2.0 / (ci * k * k)), co * ci * k * k)
+        dev = "cuda"
+        self.params = torch.from_numpy(init).to(dev)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self.wscratch = torch.empty(max(co * ci * k * k for _, ci, co, k in self.specs),
+                                    dtype=torch.float32, device=dev)
+        self._bufs = {}
+
+    # -- plumbing -----------------------------------------------------------
+    def _stream(self):
+        return C.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise GLBMError(rc, f"{what} failed")
+
+    def _wb(self, name):
+        ow, ob = self.offsets[name]
+        return ow, ob
+
+    def _conv(self, x, xbs, cin, y, ybs, cout, n, h, w, k, name, relu, xoff=0, yoff=0):
+        ow, ob = self._wb(name)
+        self._ok(self.lib.glbm_nn_conv_fwd(_ptr(x, xoff), xbs, cin, _ptr(y, yoff), ybs, cout, n, h, w, k,
+                                           _ptr(self.params, ow), _ptr(self.params, ob), int(relu),
+                                           self._stream()), "conv_fwd")
+
+    def _conv_bwd(self, x, xbs, cin, dy, dybs, cout, n, h, w, k, name, dx=None, dxbs=0):
+        ow, ob = self._wb(name)
+        self._ok(self.lib.glbm_nn_conv_bwd_weight(_ptr(x), xbs, cin, _ptr(dy), dybs, cout, n, h, w, k,
+                                                  _ptr(self.grads, ow), _ptr(self.grads, ob),
+                                                  self._stream()), "conv_bwd_weight")
+        if dx is not None:
+            self._ok(self.lib.glbm_nn_conv_bwd_data(_ptr(dy), dybs, cout, _ptr(dx), dxbs, cin, n, h, w, k,
+                                                    _ptr(self.params, ow), _ptr(self.wscratch),
+                                                    self._stream()), "conv_bwd_data")
+
+    def _relu_bwd(self, y, dy, c, n, h, w):
+        self._ok(self.lib.glbm_nn_relu_bwd(_ptr(y), c * h * w, _ptr(dy), c * h * w, c, n, h, w,
+                                           self._stream()), "relu_bwd")
+
+    def _buffers(self, n, h, w):
+        key = (n, h, w)
+        if key in self._bufs:
+            return self._bufs[key]
+        if h % 2 ** (self.levels - 1) or w % 2 ** (self.levels - 1):
+            raise ValueError(f"h, w must be multiples of {2 ** (self.levels - 1)}")
+        torch = self.torch
+        B = {}
+
+        def z(c, l):
+            return torch.empty((n, c, h >> l, w >> l), dtype=torch.float32, device="cuda")
+        L = self.levels
+        for l in range(L):
+            c = self.ch[l]
+            for nm in ("a", "e", "ga", "ge"):
+                B[f"{nm}{l}"] = z(c, l)
+            if l < L - 1:
+                B[f"p{l}"] = z(c, l + 1)
+                B[f"gp{l}"] = z(c, l + 1)
+                cc = self.ch[l + 1] + c
+                B[f"cat{l}"] = z(cc, l)
+                B[f"gcat{l}"] = z(cc, l)
+                for nm in ("da", "d", "gda", "gd"):
+                    B[f"{nm}{l}"] = z(c, l)
+        B["y"] = z(self.out_ch, 0)
+        self._bufs = {key: B}  # keep one shape at a time
+        return B
+
+    # -- network ------------------------------------------------------------
+    def forward(self, x):
+        """x: contiguous (n, in_ch, h, w) float32 CUDA tensor -> (n, out_ch, h, w)."""
+        n, _, h, w = x.shape
+        B = self._buffers(n, h, w)
+        self._x = x
+        L = self.levels
+        inp, cin = x, self.in_ch
+        for l in range(L):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            self._conv(inp, cin * hl * wl, cin, B[f"a{l}"], c * hl * wl, c, n, hl, wl, 3, f"e{l}a", True)
+            self._conv(B[f"a{l}"], c * hl * wl, c, B[f"e{l}"], c * hl * wl, c, n, hl, wl, 3, f"e{l}b", True)
+            if l < L - 1:
+                self._ok(self.lib.glbm_nn_pool2(_ptr(B[f"e{l}"]), c * hl * wl, _ptr(B[f"p{l}"]),
+                                                c * hl * wl // 4, c, n, hl, wl, 0, 0, self._stream()), "pool")
+                inp, cin = B[f"p{l}"], c
+        top, ctop = B[f"e{L - 1}"], self.ch[L - 1]
+        for l in range(L - 2, -1, -1):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            cc = ctop + c
+            cat = B[f"cat{l}"]
+            self._ok(self.lib.glbm_nn_upsample2(_ptr(top), ctop * (hl // 2) * (wl // 2), _ptr(cat), cc * hl * wl,
+                                                ctop, n, hl // 2, wl // 2, 0, self._stream()), "upsample")
+            self._ok(self.lib.glbm_nn_copy_channels(_ptr(B[f"e{l}"]), c * hl * wl, _ptr(cat, ctop * hl * wl),
+                                                    cc * hl * wl, c, n, hl, wl, 0, self._stream()), "copy")
+            self._conv(cat, cc * hl * wl, cc, B[f"da{l}"], c * hl * wl, c, n, hl, wl, 3, f"d{l}a", True)
+            self._conv(B[f"da{l}"], c * hl * wl, c, B[f"d{l}"], c * hl * wl, c, n, hl, wl, 3, f"d{l}b", True)
+            top, ctop = B[f"d{l}"], c
+        self._conv(top, ctop * h * w, ctop, B["y"], self.out_ch * h * w, self.out_ch, n, h, w, 1, "head", False)
+        return B["y"]
+
+    def backward(self, gy):
+        """Gradients of the loss w.r.t. the parameters (into self.grads) given
+        gy = dL/dy of the last forward call."""
+        x = self._x
+        n, _, h, w = x.shape
+        B = self._buffers(n, h, w)
+        L = self.levels
+        self.grads.zero_()
+        top = B["d0"] if L > 1 else B["e0"]
+        gtop = B["gd0"] if L > 1 else B["ge0"]
+        c0 = self.ch[0]
+        self._conv_bwd(top, c0 * h * w, c0, gy, self.out_ch * h * w, self.out_ch, n, h, w, 1, "head",
+                       dx=gtop, dxbs=c0 * h * w)
+        for l in range(0, L - 1):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            cup = self.ch[l + 1]
+            cc = cup + c
+            self._relu_bwd(B[f"d{l}"], B[f"gd{l}"], c, n, hl, wl)
+            self._conv_bwd(B[f"da{l}"], c * hl * wl, c, B[f"gd{l}"], c * hl * wl, c, n, hl, wl, 3, f"d{l}b",
+                           dx=B[f"gda{l}"], dxbs=c * hl * wl)
+            self._relu_bwd(B[f"da{l}"], B[f"gda{l}"], c, n, hl, wl)
+            self._conv_bwd(B[f"cat{l}"], cc * hl * wl, cc, B[f"gda{l}"], c * hl * wl, c, n, hl, wl, 3, f"d{l}a",
+                           dx=B[f"gcat{l}"], dxbs=cc * hl * wl)
+            gcat = B[f"gcat{l}"]
+            self._ok(self.lib.glbm_nn_copy_channels(_ptr(gcat, cup * hl * wl), cc * hl * wl, _ptr(B[f"ge{l}"]),
+                                                    c * hl * wl, c, n, hl, wl, 0, self._stream()), "copy")
+            dst = B[f"ge{L - 1}"] if l + 1 == L - 1 else B[f"gd{l + 1}"]
+            self._ok(self.lib.glbm_nn_upsample2(_ptr(gcat), cc * hl * wl, _ptr(dst), cup * (hl // 2) * (wl // 2),
+                                                cup, n, hl // 2, wl // 2, 1, self._stream()), "upsample_bwd")
+        for l in range(L - 1, -1, -1):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            if l < L - 1:
+                self._ok(self.lib.glbm_nn_pool2(_ptr(B[f"gp{l}"]), c * hl * wl // 4, _ptr(B[f"ge{l}"]),
+                                                c * hl * wl, c, n, hl, wl, 1, 1, self._stream()), "pool_bwd")
+            self._relu_bwd(B[f"e{l}"], B[f"ge{l}"], c, n, hl, wl)
+            self._conv_bwd(B[f"a{l}"], c * hl * wl, c, B[f"ge{l}"], c * hl * wl, c, n, hl, wl, 3, f"e{l}b",
+                           dx=B[f"ga{l}"], dxbs=c * hl * wl)
+            self._relu_bwd(B[f"a{l}"], B[f"ga{l}"], c, n, hl, wl)
+            if l == 0:
+                self._conv_bwd(x, self.in_ch * h * w, self.in_ch, B["ga0"], c * h * w, c, n, h, w, 3, "e0a")
+            else:
+                cp = self.ch[l - 1]
+                self._conv_bwd(B[f"p{l - 1}"], cp * hl * wl, cp, B[f"ga{l}"], c * hl * wl, c, n, hl, wl, 3,
+                               f"e{l}a", dx=B[f"gp{l - 1}"], dxbs=cp * hl * wl)
+
+    def loss(self, pred, target, channel_weight, with_grad=True):
+        torch = self.torch
+        n, c, h, w = pred.shape
+        cw = torch.as_tensor(channel_weight, dtype=torch.float32, device="cuda")
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(pred) if with_grad else None
+        self._ok(self.lib.glbm_nn_mse(_ptr(pred), _ptr(target), _ptr(cw), c, n, h, w,
+                                      _ptr(g) if g is not None else None, C.c_void_p(out.data_ptr()),
+                                      self._stream()), "mse")
+        return out, g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.t += 1
+        self._ok(self.lib.glbm_nn_adam(_ptr(self.params), _ptr(self.grads), _ptr(self.m), _ptr(self.v),
+                                       self.nparams, float(lr), float(beta1), float(beta2), float(eps), self.t,
+                                       self._stream()), "adam")
+
+    def save(self, path):
+        np.save(path, self.params.cpu().numpy())
+
+    def load(self, path):
+        self.params.copy_(self.torch.from_numpy(np.load(path)).cuda())
+
+
+# -- data --------------------------------------------------------------------
+
+def features(eps, K, G):
+    """Network input (3, ny, nx) float32 from one medium."""
+    f = np.empty((3,) + eps.shape, dtype=np.float32)
+    f[0] = (eps - 0.05) / 0.05
+    f[1] = (np.log10(K) + 2.0) / 2.0
+    f[2] = np.log10(abs(G)) + 6.0
+    return f
+
+
+def targets(rho, ux, uy, K, G, nu):
+    t = np.empty((3,) + rho.shape, dtype=np.float32)
+    t[0] = (rho - 1.0) / (G * RHO_SCALE)
+    t[1] = ux * nu / (K * G)
+    t[2] = uy * nu / (K * G)
+    return t
+
+
+def decode(y, K, G, nu):
+    """Network output (3, ny, nx) -> (rho, ux, uy) FP64."""
+    y = np.asarray(y, dtype=np.float64)
+    return 1.0 + y[0] * G * RHO_SCALE, y[1] * K * G / nu, y[2] * K * G / nu
