@@ -309,6 +309,28 @@ double glbm_qsat_from_langmuir_volume(double qsat_b, double rho_b, double eps,
 const char *glbm_last_error(glbm_t h);
 
 /* ===========================================================================
+ * EM fit of a one-dimensional Gaussian mixture (Sec. 2.2, Eqs. 20-24), the
+ * paper's way of splitting a measured pore-size distribution into OM and IOM
+ * components.  Each iteration computes the E-step responsibilities (Eqs.
+ * 20-21; Eq. 21 read with the minus sign its exponent lacks as printed) and
+ * the M-step fractions, means and variances (Eqs. 22-24; Eq. 24 with the
+ * means just updated), in FP64 with deterministic reductions.
+ *   x              m samples (host or device per device_ptrs)
+ *   k              components, 1..8
+ *   phi, mu, var   host arrays of k: initial guess in, estimate out
+ *   max_iter, tol  stop after max_iter iterations or when the mean
+ *                  log-likelihood changes by less than tol (tol <= 0: never)
+ *   iters, loglik  iterations done and the mean log-likelihood of the last
+ *                  E-step (either may be NULL)
+ * EINVAL (message in glbm_last_error(NULL)) for bad sizes or non-positive
+ * initial fractions/variances.
+ * ======================================================================== */
+glbm_status glbm_em_gmm1d(const double *x, long long m, int k, double *phi,
+                          double *mu, double *var, int max_iter, double tol,
+                          int *iters, double *loglik, int device_ptrs,
+                          void *stream);
+
+/* ===========================================================================
  * Network kernels of the learned warm start.  The paper has no surrogate:
  * these exist so that a small U-Net, trained by this library on the solver's
  * own converged fields, can predict the steady density deviation and

@@ -103,6 +103,8 @@ def _lib(omp: bool = False) -> C.CDLL:
             lib.orc_kapp.argtypes = [_D] * 7 + [C.c_int] + [_D] * 3
             lib.orc_qsat_from_langmuir_volume.restype = _D
             lib.orc_qsat_from_langmuir_volume.argtypes = [_D] * 6
+            lib.orc_em_gmm1d.restype = C.c_int
+            lib.orc_em_gmm1d.argtypes = [_PD, C.c_long, C.c_int, _PD, _PD, _PD, C.c_int, _D, _PD]
             lib.orc_kapp_field.argtypes = [_PD, C.POINTER(C.c_ubyte), _PD, C.c_long] + [_D] * 9 + [_PD]
             _LIBS[omp] = lib
         return _LIBS[omp]
@@ -216,6 +218,21 @@ def kapp_field(r, organic, eps, P, T, eta, tort, qsat, b, Ds, dx, M=METHANE_M):
                           _ptr(e), r.size, P, T, M, eta, tort, qsat, b, Ds, dx,
                           _ptr(K))
     return K
+
+
+# -- EM for a 1-D Gaussian mixture (Sec. 2.2) ----------------------------------
+
+def em_gmm1d(x, phi, mu, var, max_iter=500, tol=0.0):
+    """Eqs. 20-24 from the initial guess (phi, mu, var) -> (phi, mu, var,
+    iterations, mean log-likelihood of the last E-step)."""
+    x = _f64(x).ravel()
+    phi, mu, var = (np.array(a, dtype=np.float64) for a in (phi, mu, var))
+    ll = _D()
+    it = _lib().orc_em_gmm1d(_ptr(x), x.size, phi.size, _ptr(phi), _ptr(mu), _ptr(var),
+                             int(max_iter), float(tol), C.byref(ll))
+    if it < 0:
+        raise ValueError("orc_em_gmm1d: bad arguments")
+    return phi, mu, var, it, ll.value
 
 
 class Oracle:

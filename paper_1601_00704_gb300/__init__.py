@@ -19,7 +19,7 @@ import numpy as np
 
 from .build import LIB as LIB_PATH
 
-__all__ = ["Solver", "Batch", "kapp_field", "GLBMError", "load", "F32", "F64",
+__all__ = ["Solver", "Batch", "kapp_field", "em_gmm1d", "GLBMError", "load", "F32", "F64",
            "F16DEV", "BF16DEV", "WALLS_Y", "PERIODIC_Y", "NEAREST16", "STORAGE"]
 
 F32, F64, F16DEV, BF16DEV = 0, 1, 2, 3
@@ -43,7 +43,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_batch_get_fields",
            "glbm_nn_conv_fwd", "glbm_nn_conv_bwd_data", "glbm_nn_conv_bwd_weight",
            "glbm_nn_relu_bwd", "glbm_nn_copy_channels", "glbm_nn_pool2",
-           "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam"]
+           "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam", "glbm_em_gmm1d"]
 
 
 class GLBMError(RuntimeError):
@@ -109,6 +109,7 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_nn_mse": ([_VP, _VP, _VP, i, i, i, i, _VP, _VP, _VP], i),
         "glbm_nn_adam": ([_VP, _VP, _VP, _VP, ll, C.c_float, C.c_float, C.c_float,
                           C.c_float, i, _VP], i),
+        "glbm_em_gmm1d": ([_VP, ll, i, _PD, _PD, _PD, i, d, C.POINTER(i), _PD, i, _VP], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -370,6 +371,27 @@ class Batch:
         self._check(self._lib.glbm_batch_info(self._h, C.byref(t), C.byref(o), C.byref(l),
                                               C.byref(nn)))
         return {"threads": t.value, "order": o.value, "launches": l.value, "nodes": nn.value}
+
+
+def em_gmm1d(x, phi, mu, var, max_iter=500, tol=1e-12):
+    """EM fit of a 1-D Gaussian mixture on the GPU (Eqs. 20-24) -> (phi, mu,
+    var, iterations, mean log-likelihood).  x: NumPy array or CUDA tensor."""
+    lib = load()
+    k = len(phi)
+    p, u, v = ((C.c_double * k)(*map(float, a)) for a in (phi, mu, var))
+    it, llv = C.c_int(), C.c_double()
+    if _is_tensor(x) and x.is_cuda:
+        import torch
+        xs = x.to(torch.float64).contiguous()
+        ptr, dev, n = xs.data_ptr(), 1, xs.numel()
+    else:
+        xs = np.ascontiguousarray(x, dtype=np.float64).ravel()
+        ptr, dev, n = xs.ctypes.data, 0, xs.size
+    rc = lib.glbm_em_gmm1d(ptr, n, k, p, u, v, int(max_iter), float(tol), C.byref(it),
+                           C.byref(llv), dev, None)
+    if rc != 0:
+        raise GLBMError(rc, lib.glbm_last_error(None).decode())
+    return np.array(p[:]), np.array(u[:]), np.array(v[:]), it.value, llv.value
 
 
 def qsat_from_langmuir_volume(qsat_b, rho_b, eps, toc, rho_ch4, M_ch4=0.01604):

@@ -8,7 +8,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu", "nn.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu", "nn.cu", "em.cu")]
 HDR = [os.path.join(HERE, "csrc", "glbm_kernels.cuh")]
 OBJ = os.path.join(HERE, "csrc", "_obj")
 INCLUDE = os.path.join(ROOT, "include")

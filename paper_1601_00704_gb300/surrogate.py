@@ -29,7 +29,7 @@ import numpy as np
 
 from . import GLBMError, load
 
-RHO_SCALE = 30.0
+RHO_SCALE = 0.3
 
 
 def _ptr(t, offset_floats=0):
@@ -42,12 +42,12 @@ class UNet:
     concatenation, and a 1x1 head.  FP32 parameters in one flat device
     vector (layout of ``layer_specs``)."""
 
-    def __init__(self, in_ch=3, out_ch=3, base=32, levels=4, seed=0):
+    def __init__(self, in_ch=3, out_ch=3, base=32, levels=4, seed=0, max_ch=None):
         import torch
         self.torch = torch
         self.lib = load()
         self.in_ch, self.out_ch, self.base, self.levels = in_ch, out_ch, base, levels
-        self.ch = [base * 2 ** l for l in range(levels)]
+        self.ch = [base * 2 ** l if not max_ch else min(base * 2 ** l, max_ch) for l in range(levels)]
         self.specs = []
         cin = in_ch
         for l in range(levels):
@@ -225,17 +225,60 @@ class UNet:
                                       self._stream()), "mse")
         return out, g
 
+    def coarse_loss(self, pred, target, factor, weight, grad):
+        """Adds weight * mean((pool^k pred_0 - pool^k target_0)^2), k = log2(factor),
+        of the first channel to the loss, and its gradient to grad (channel 0).
+        Emphasises the large-scale density field that the slow pressure modes
+        carry.  Returns the device loss."""
+        torch = self.torch
+        n, c, h, w = pred.shape
+        steps = int(round(np.log2(factor)))
+        p_prev, t_prev, ps, ts = pred, target, [], []
+        hh, ww, sb = h, w, c * h * w
+        for _ in range(steps):
+            p_new = torch.empty((n, 1, hh // 2, ww // 2), dtype=torch.float32, device="cuda")
+            t_new = torch.empty_like(p_new)
+            for src, dst in ((p_prev, p_new), (t_prev, t_new)):
+                self._ok(self.lib.glbm_nn_pool2(_ptr(src), sb, _ptr(dst), hh * ww // 4, 1, n, hh, ww, 0, 0,
+                                                self._stream()), "pool")
+            ps.append((p_new, hh, ww))
+            p_prev, t_prev, sb = p_new, t_new, hh * ww // 4
+            hh, ww = hh // 2, ww // 2
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        cw = torch.tensor([weight], dtype=torch.float32, device="cuda")
+        g = torch.empty_like(p_prev)
+        self._ok(self.lib.glbm_nn_mse(_ptr(p_prev), _ptr(t_prev), _ptr(cw), 1, n, hh, ww, _ptr(g),
+                                      C.c_void_p(loss.data_ptr()), self._stream()), "mse")
+        # back through the pools; the last one accumulates into grad[:, 0]
+        for k in range(steps - 1, -1, -1):
+            _, h_in, w_in = ps[k]
+            if k == 0:
+                self._ok(self.lib.glbm_nn_pool2(_ptr(g), h_in * w_in // 4, _ptr(grad), c * h_in * w_in, 1, n,
+                                                h_in, w_in, 1, 1, self._stream()), "pool_bwd")
+            else:
+                g_up = torch.empty((n, 1, h_in, w_in), dtype=torch.float32, device="cuda")
+                self._ok(self.lib.glbm_nn_pool2(_ptr(g), h_in * w_in // 4, _ptr(g_up), h_in * w_in, 1, n, h_in,
+                                                w_in, 1, 0, self._stream()), "pool_bwd")
+                g = g_up
+        return loss
+
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self.t += 1
         self._ok(self.lib.glbm_nn_adam(_ptr(self.params), _ptr(self.grads), _ptr(self.m), _ptr(self.v),
                                        self.nparams, float(lr), float(beta1), float(beta2), float(eps), self.t,
                                        self._stream()), "adam")
 
-    def save(self, path):
-        np.save(path, self.params.cpu().numpy())
+    def save(self, path, half=False):
+        """Parameters as .npy (FP16 when half: the network still computes in
+        FP32; the rounding is far below the prediction error)."""
+        p = self.params.cpu().numpy()
+        np.save(path, p.astype(np.float16) if half else p)
 
     def load(self, path):
-        self.params.copy_(self.torch.from_numpy(np.load(path)).cuda())
+        p = np.load(path).astype(np.float32)
+        if p.size != self.nparams:
+            raise ValueError(f"{path}: {p.size} parameters, this network has {self.nparams}")
+        self.params.copy_(self.torch.from_numpy(p).cuda())
 
 
 # -- data --------------------------------------------------------------------

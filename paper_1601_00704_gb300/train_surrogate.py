@@ -1,0 +1,267 @@
+"""Train the warm-start U-Net on the solver's own converged solutions.
+
+    python -m paper_1601_00704_gb300.train_surrogate [--count 2000 --n 256 ...]
+
+1. Media: ``media.shale_batch`` (OM/IOM maps, lognormal pore radii, pressure
+   and Langmuir parameters drawn per medium), per-node K from the DGM/GMS
+   model (``glbm_kapp_field``), all at n x n.
+2. Labels: every medium advanced together in one ``Batch`` (FP32) until its
+   mean velocity changes by less than ``--tol`` per ``--check`` steps (or
+   ``--max-steps``); density and velocity exported per medium.
+3. Training: Adam on the weighted MSE of (delta rho, u_x, u_y), with the
+   mirror symmetries of the linear (Darcy) regime as augmentation:
+   y-mirror maps (rho, ux, uy) -> (rho, ux, -uy); x-mirror maps them to
+   (-(rho-1), ux, -uy) about rho = 1.
+4. Output: the flat FP32 parameter vector (.npy) and a JSON record of the
+   recipe, the label convergence and the loss history.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# physical inputs of the DGM/GMS sweep (the paper's shale-matrix table where
+# it gives them; methane at 350 K)
+DX, T_GAS, ETA, TORT, DS = 7.8125e-9, 350.0, 18.231e-6, 2.0, 1e-8
+RHO_KEROGEN, EPS_KEROGEN, RHO_CH4 = 1.65e3, 0.2, 0.717
+G = 1e-6
+TAU = 1.0
+NU = (TAU - 0.5) / 3.0
+CHANNEL_WEIGHT = (1.0, 0.1, 0.1)
+DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "unet_b32_l6_c128.npy")
+
+
+def medium_k(pkg, m):
+    qsat = pkg.qsat_from_langmuir_volume(m["V_L"], RHO_KEROGEN, EPS_KEROGEN, max(m["toc"], 1e-9), RHO_CH4)
+    return pkg.kapp_field(m["r"], m["organic"], m["eps"], m["P"], T_GAS, ETA, TORT, qsat, 1.0 / m["P_L"],
+                          DS, DX)
+
+
+def make_dataset(count, n, seed, tol, check, max_steps, log=print):
+    import media
+    import paper_1601_00704_gb300 as pkg
+    from paper_1601_00704_gb300 import surrogate
+    t0 = time.perf_counter()
+    specs = media.shale_batch(count, seed=seed, sides=(n,))
+    Ks = [medium_k(pkg, m) for m in specs]
+    b = pkg.Batch([(n, n)] * count, tau=TAU, storage="f32")
+    for i, (m, K) in enumerate(zip(specs, Ks)):
+        b.set_medium(i, m["eps"], K)
+    b.set_force(G)
+    steps, left = b.step(max_steps, tol=tol, check_every=check)
+    res = b.results()
+    X = np.empty((count, 3, n, n), np.float32)
+    Y = np.empty((count, 3, n, n), np.float32)
+    for i, (m, K) in enumerate(zip(specs, Ks)):
+        rho, ux, uy = b.fields(i)
+        X[i] = surrogate.features(m["eps"], K, G)
+        Y[i] = surrogate.targets(rho, ux, uy, K, G, NU)
+    b.close()
+    info = {"count": count, "n": n, "seed": seed, "tol": tol, "check": check, "max_steps": max_steps,
+            "steps_run": int(steps), "not_converged": int(left),
+            "median_steps": float(np.median(res["steps"])), "seconds": time.perf_counter() - t0}
+    log(f"dataset: {info}")
+    return X, Y, info
+
+
+def augment(x, y, rng):
+    """Exact mirror symmetries of the linear regime (see module docstring)."""
+    if rng.random() < 0.5:   # y-mirror (walls are symmetric)
+        x = x[..., ::-1, :]
+        y = y[..., ::-1, :].copy()
+        y[:, 2] = -y[:, 2]
+    if rng.random() < 0.5:   # x-mirror with the force kept along +x
+        x = x[..., ::-1]
+        y = y[..., ::-1].copy()
+        y[:, 0] = -y[:, 0]
+        y[:, 2] = -y[:, 2]
+    return np.ascontiguousarray(x), np.ascontiguousarray(y)
+
+
+def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0)):
+    """X, Y: one (count, 3, n, n) array pair, or lists of pairs of different
+    sizes (each batch is drawn from one size; sizes interleave)."""
+    if not isinstance(X, (list, tuple)):
+        X, Y = [X], [Y]
+    import torch
+    rng = np.random.default_rng(seed)
+    hist = []
+    total = epochs * sum((len(x) + batch - 1) // batch for x in X)
+    it = 0
+    t0 = time.perf_counter()
+    for ep in range(epochs):
+        jobs = []
+        for k, x in enumerate(X):
+            order = rng.permutation(len(x))
+            jobs += [(k, order[s:s + batch]) for s in range(0, len(x), batch)]
+        jobs = [jobs[i] for i in rng.permutation(len(jobs))]
+        acc, cnt = 0.0, 0
+        for k, idx in jobs:
+            xb, yb = augment(X[k][idx], Y[k][idx], rng)
+            tx = torch.from_numpy(xb).cuda()
+            ty = torch.from_numpy(yb).cuda()
+            # cosine learning-rate decay
+            lr_t = 0.5 * lr * (1 + np.cos(np.pi * it / total))
+            pred = net.forward(tx)
+            loss, g = net.loss(pred, ty, CHANNEL_WEIGHT)
+            if coarse:
+                loss = loss + net.coarse_loss(pred, ty, coarse[0], coarse[1], g)
+            net.backward(g)
+            net.adam_step(lr_t)
+            acc += float(loss.item()) * len(idx)
+            cnt += len(idx)
+            it += 1
+        hist.append(acc / cnt)
+        log(f"epoch {ep + 1}/{epochs}: loss {hist[-1]:.5f} ({time.perf_counter() - t0:.0f} s)")
+    return hist
+
+
+def predict(net, eps, K):
+    """Warm-start fields (rho, ux, uy) for one medium of any size (multiple
+    of 2^(levels-1))."""
+    import torch
+
+    from paper_1601_00704_gb300 import surrogate
+    x = torch.from_numpy(surrogate.features(eps, K, G)[None]).cuda()
+    y = net.forward(x).cpu().numpy()[0]
+    return surrogate.decode(y, K, G, NU)
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--count", type=int, default=2000)
+    p.add_argument("--n", type=int, default=256)
+    p.add_argument("--count2", type=int, default=0, help="extra media at --n2 (multi-size training)")
+    p.add_argument("--n2", type=int, default=512)
+    p.add_argument("--seed", type=int, default=1000)
+    p.add_argument("--tol", type=float, default=1e-5)
+    p.add_argument("--check", type=int, default=1000)
+    p.add_argument("--max-steps", type=int, default=60000)
+    p.add_argument("--epochs", type=int, default=8)
+    p.add_argument("--batch", type=int, default=8)
+    p.add_argument("--lr", type=float, default=1e-3)
+    p.add_argument("--base", type=int, default=32)
+    p.add_argument("--levels", type=int, default=6)
+    p.add_argument("--max-ch", type=int, default=128)
+    p.add_argument("--coarse", type=float, default=4.0, help="weight of the 8x-pooled density loss (0: off)")
+    p.add_argument("--out", default=DEFAULT_WEIGHTS)
+    p.add_argument("--study", action="store_true", help="run the 2048^2 warm-start study after training")
+    p.add_argument("--study-only", metavar="WEIGHTS", help="load these weights and only run the study")
+    a = p.parse_args(argv)
+    from paper_1601_00704_gb300 import build
+    build.build()
+    from paper_1601_00704_gb300 import surrogate
+    if a.study_only:
+        net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)
+        net.load(a.study_only)
+        print(json.dumps(warm_start_study(net)))
+        return
+    X, Y, info = make_dataset(a.count, a.n, a.seed, a.tol, a.check, a.max_steps)
+    if a.count2:
+        X2, Y2, info2 = make_dataset(a.count2, a.n2, a.seed + 1, a.tol, a.check, 3 * a.max_steps)
+        X, Y, info = [X, X2], [Y, Y2], [info, info2]
+    net = surrogate.UNet(base=a.base, levels=a.levels, seed=a.seed, max_ch=a.max_ch)
+    t0 = time.perf_counter()
+    hist = train(net, X, Y, a.epochs, a.batch, a.lr, seed=a.seed,
+                 coarse=(8, a.coarse) if a.coarse > 0 else None)
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    net.save(a.out, half=True)
+    rec = {"dataset": info, "epochs": a.epochs, "batch": a.batch, "lr": a.lr, "base": a.base,
+           "levels": a.levels, "max_ch": a.max_ch, "coarse_weight": a.coarse, "channel_weight": CHANNEL_WEIGHT, "loss": hist,
+           "train_seconds": time.perf_counter() - t0, "params": int(net.nparams)}
+    with open(os.path.splitext(a.out)[0] + ".json", "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps({k: v for k, v in rec.items() if k != "loss"}))
+    if a.study:
+        rec["warm_start_study"] = warm_start_study(net)
+        with open(os.path.splitext(a.out)[0] + ".json", "w") as fh:
+            json.dump(rec, fh, indent=1)
+
+
+
+def time_to_k(pkg, eps, K, k_ref, storage="f32", init=None, check=1000, crit=1e-3, max_steps=3_000_000):
+    """Steps and CUDA-event seconds until |K_app/k_ref - 1| <= crit, from rest
+    or from init = (rho, ux, uy) (the initialisation is inside the timing)."""
+    import torch
+    stream = torch.cuda.Stream()
+    n = eps.shape[0]
+    s = pkg.Solver(eps.shape[1], n, tau=TAU, storage=storage, stream=stream)
+    s.set_medium(eps, K)
+    s.set_force(G)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if init is not None:
+        s.init_equilibrium(*init)
+    steps, k = 0, float("nan")
+    while steps < max_steps:
+        s.step(check)
+        steps += check
+        k = s.permeability()
+        if abs(k / k_ref - 1) <= crit:
+            break
+    e1.record(stream)
+    e1.synchronize()
+    out = {"steps": steps, "seconds": e0.elapsed_time(e1) * 1e-3, "k_app": k, "rel_err": k / k_ref - 1,
+           "met": abs(k / k_ref - 1) <= crit}
+    s.close()
+    return out
+
+
+def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
+    """Cold vs surrogate-started runs on an unseen n x n medium of the
+    training recipe: steps and time to |K_app/K_ref - 1| <= 1e-3 (K_ref: FP32
+    run to relative change < ref_tol per 10^4 steps), plus the raw
+    surrogate's own K_app error."""
+    import torch
+
+    import media
+    import paper_1601_00704_gb300 as pkg
+    m = media.shale_batch(1, seed=seed, sides=(n,))[0]
+    K = medium_k(pkg, m)
+    ref = pkg.Solver(n, n, tau=TAU)
+    ref.set_medium(m["eps"], K)
+    ref.set_force(G)
+    t0 = time.perf_counter()
+    ref_steps, conv = ref.step(3_000_000, tol=ref_tol, check_every=10000)
+    k_ref = ref.permeability()
+    ref_s = time.perf_counter() - t0
+    ref.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rho, ux, uy = predict(net, m["eps"], K)
+    torch.cuda.synchronize()
+    infer_s = time.perf_counter() - t0
+    k_raw = NU * float(np.mean(ux)) / G
+    runs = {"cold_f32": time_to_k(pkg, m["eps"], K, k_ref),
+            "warm_f32": time_to_k(pkg, m["eps"], K, k_ref, init=(rho, ux, uy)),
+            "cold_bf16": time_to_k(pkg, m["eps"], K, k_ref, storage="bf16"),
+            "warm_bf16": time_to_k(pkg, m["eps"], K, k_ref, storage="bf16", init=(rho, ux, uy))}
+    for r in ("warm_f32", "warm_bf16"):
+        runs[r]["seconds_with_inference"] = runs[r]["seconds"] + infer_s
+    base = runs["cold_f32"]["seconds"]
+    out = {"workload": f"{n}x{n} medium of the training recipe, unseen seed {seed} (P {m['P'] / 1e6:.1f} MPa)",
+           "k_ref": k_ref, "k_ref_from": f"FP32 cold run to relative change < {ref_tol:g} per 1e4 steps "
+                                         f"({ref_steps} steps, converged={conv}, {ref_s:.1f} s)",
+           "criterion": "|K_app/K_ref - 1| <= 1e-3, checked every 1000 steps",
+           "surrogate_raw_k_app_rel_err": k_raw / k_ref - 1, "inference_s": infer_s, "runs": runs,
+           "speedup_vs_cold_f32": {r: base / v.get("seconds_with_inference", v["seconds"])
+                                   for r, v in runs.items() if v["met"] and r != "cold_f32"}}
+    log(json.dumps(out))
+    return out
+
+
+if __name__ == "__main__":
+    main()
