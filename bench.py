@@ -75,6 +75,8 @@ def args_():
                    help="skip the time-to-permeability comparison")
     p.add_argument("--ttp-n", type=int, default=1024,
                    help="lattice side of the time-to-permeability runs")
+    p.add_argument("--no-warm", action="store_true",
+                   help="skip the learned warm-start study")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-media (DGM/GMS sweep) measurement")
     p.add_argument("--batch-count", type=int, default=512)
@@ -446,6 +448,25 @@ def batch_bench(a):
     }
 
 
+# -- learned warm start ---------------------------------------------------------
+
+def warm_start(a):
+    """Cold vs surrogate-initialised runs (FP32 and BF16) on an unseen 2048^2
+    medium of the surrogate's training recipe, with the committed weights."""
+    from paper_1601_00704_gb300 import surrogate
+    from paper_1601_00704_gb300 import train_surrogate as T
+    path = T.DEFAULT_WEIGHTS
+    if not os.path.exists(path):
+        return {"unavailable": f"no trained weights at {os.path.relpath(path, ROOT)}"}
+    meta = json.load(open(os.path.splitext(path)[0] + ".json"))
+    net = surrogate.UNet(base=meta["base"], levels=meta["levels"], max_ch=meta.get("max_ch"))
+    net.load(path)
+    out = T.warm_start_study(net, log=lambda *_: None)
+    out["network"] = {"levels": meta["levels"], "base": meta["base"], "max_ch": meta.get("max_ch"),
+                      "params": meta["params"], "weights": os.path.relpath(path, ROOT)}
+    return out
+
+
 # -- arms ---------------------------------------------------------------------
 
 def run_reference(a, world, rank):
@@ -566,11 +587,13 @@ def run_ours(a, world, rank, local):
     s.close()
     # single-GPU studies (skipped under torchrun, where only the scaling
     # measurement above is wanted)
-    ttp = batch = formats = None
+    ttp = batch = formats = warm = None
     if world == 1:
         formats = format_throughput(a, eps, K)
         if not a.no_ttp:
             ttp = time_to_permeability(a)
+        if not a.no_warm:
+            warm = warm_start(a)
         if not a.no_batch:
             batch = batch_bench(a)
     if rank == 0:
@@ -585,6 +608,7 @@ def run_ours(a, world, rank, local):
             "gpu_launches": l1 - l0, "k_app": kapp,
             "storage_formats": formats,
             "time_to_permeability": ttp,
+            "warm_start": warm,
             "batch": batch,
         }
         print(json.dumps(line), flush=True)
