@@ -24,7 +24,7 @@ def test_em_matches_oracle(pkg, orc, m, k):
     w /= w.sum()
     lab = rng.choice(k, size=m, p=w)
     x = np.array([comps[j][0] for j in lab]) + rng.standard_normal(m) * np.array([comps[j][1] for j in lab])
-    init = (np.full(k, 1.0 / k), np.linspace(x.min() + 1, x.max() - 1, k), np.full(k, x.var()))
+    init = (np.full(k, 1.0 / k), np.linspace(x.min() + 1, x.max() - 1, k), np.full(k, max(x.var(), 1.0)))
     for it in (1, 5, 40):
         a = pkg.em_gmm1d(x, *init, max_iter=it, tol=0.0)
         b = orc.em_gmm1d(x, *init, max_iter=it, tol=0.0)
