@@ -323,7 +323,9 @@ const char *glbm_last_error(glbm_t h);
  *   iters, loglik  iterations done and the mean log-likelihood of the last
  *                  E-step (either may be NULL)
  * EINVAL (message in glbm_last_error(NULL)) for bad sizes or non-positive
- * initial fractions/variances.
+ * initial fractions/variances; ENAN when the estimate is no longer finite
+ * (a component collapsed onto one sample: zero variance), with the
+ * arrays still written.
  * ======================================================================== */
 glbm_status glbm_em_gmm1d(const double *x, long long m, int k, double *phi,
                           double *mu, double *var, int max_iter, double tol,

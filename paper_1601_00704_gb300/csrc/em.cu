@@ -212,12 +212,17 @@ extern "C" glbm_status glbm_em_gmm1d(const double *x, long long m, int k, double
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (e != cudaSuccess) return emfail(GLBM_ECUDA, "em_gmm1d: %s", cudaGetErrorString(e));
+    bool finite = true;
     for (int j = 0; j < k; ++j) {
         phi[j] = hp.phi[j];
         mu[j] = hp.mu[j];
         var[j] = hp.var[j];
+        finite = finite && std::isfinite(phi[j]) && std::isfinite(mu[j]) && std::isfinite(var[j]);
     }
     if (iters) *iters = it;
     if (loglik) *loglik = max_iter > 0 ? ll : NAN;
+    // a component that collapses onto a single sample has zero variance and
+    // the next E-step is undefined
+    if (!finite) return emfail(GLBM_ENAN, "em_gmm1d: %s", "estimate not finite (a component collapsed)");
     return GLBM_OK;
 }

@@ -53,6 +53,17 @@ struct glbm {
     uint32_t seed = 0x2545F491u;
     long long tstep = 0;      // time steps launched since the last reset
     long long steps = 0, launches = 0;
+    // chunks replayed from captured CUDA graphs (FP32/FP64 on a non-legacy
+    // stream): key = (buffer parity at start, steps, reduce at end, test)
+    struct Graph {
+        int parity;
+        long long chunk;
+        int reduce, test;
+        double tol;
+        cudaGraphExec_t exec;
+    };
+    Graph graphs[8];
+    int ngraphs = 0;
     char err[512] = "";
 };
 
@@ -177,6 +188,53 @@ glbm_status read_status(glbm *h) {
 glbm_status reset_status(glbm *h) {
     CU(h, cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), h->stream));
     h->reduced = false;
+    return GLBM_OK;
+}
+
+void drop_graphs(glbm *h) {
+    for (int i = 0; i < h->ngraphs; ++i) cudaGraphExecDestroy(h->graphs[i].exec);
+    h->ngraphs = 0;
+}
+
+bool graph_eligible(const glbm *h) {
+    return h->stream != nullptr && (h->storage == GLBM_F32 || h->storage == GLBM_F64);
+}
+
+// Enqueue one chunk (chunk steps, the last one reducing when `reduce`, then
+// the finalize), directly or by replaying a captured graph of it.
+glbm_status run_chunk(glbm *h, long long chunk, bool reduce, double tol) {
+    const int test = tol > 0.0;
+    if (graph_eligible(h) && chunk >= 4) {
+        for (int i = 0; i < h->ngraphs; ++i) {
+            const glbm::Graph &g = h->graphs[i];
+            if (g.parity == h->cur && g.chunk == chunk && g.reduce == int(reduce) && g.test == test && g.tol == tol) {
+                CU(h, cudaGraphLaunch(g.exec, h->stream));
+                h->launches += chunk + (reduce ? 1 : 0);
+                h->tstep += chunk;
+                if (chunk % 2) h->cur ^= 1;
+                if (reduce) h->reduced = true;
+                return GLBM_OK;
+            }
+        }
+        if (h->ngraphs == 8) drop_graphs(h);
+        const int p0 = h->cur;
+        cudaGraph_t graph = nullptr;
+        CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        for (long long s = 0; s < chunk; ++s) do_step(h, reduce && s == chunk - 1);
+        if (reduce) finalize(h, tol);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "step: graph capture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "step: graph instantiate failed: %s", cudaGetErrorString(e));
+        h->graphs[h->ngraphs++] = {p0, chunk, int(reduce), test, tol, exec};
+        CU(h, cudaGraphLaunch(exec, h->stream));
+        return GLBM_OK;
+    }
+    for (long long s = 0; s < chunk; ++s)
+        if (glbm_status st = do_step(h, reduce && s == chunk - 1)) return st;
+    if (reduce) finalize(h, tol);
     return GLBM_OK;
 }
 
@@ -308,6 +366,7 @@ glbm_status launch_error(glbm *h) {
 }
 
 void release(glbm *h) {
+    drop_graphs(h);
     for (auto &p : h->buf) if (p) cudaFree(p), p = nullptr;
     for (auto &p : h->coef) if (p) cudaFree(p), p = nullptr;
     if (h->partial) cudaFree(h->partial), h->partial = nullptr;
@@ -406,6 +465,7 @@ glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K, double
     CU(h, cudaMemsetAsync(h->buf[0], 0, size_t(9) * h->plane * h->elem, h->stream));
     CU(h, cudaMemsetAsync(h->buf[1], 0, size_t(9) * h->plane * h->elem, h->stream));
     if (glbm_status s = reset_status(h)) return s;
+    drop_graphs(h);  // the Forchheimer switch may change the kernel
     h->cur = 0;
     h->steps = 0;
     h->tstep = 0;
@@ -422,6 +482,7 @@ glbm_status glbm_set_force(glbm_t h, double gx, double gy) {
     if (!std::isfinite(gx) || !std::isfinite(gy)) return fail(h, GLBM_EINVAL, "set_force: G must be finite");
     h->gx = gx;
     h->gy = gy;
+    drop_graphs(h);  // G is baked into captured launches
     // FP16 at rest: start with |g*S| ~ 2^8 per unit of G (the first steps'
     // deviations are O(eps*G)); later chunks adapt S to the stored maximum
     if (h->storage == GLBM_F16DEV && h->at_rest && (gx != 0.0 || gy != 0.0))
@@ -491,13 +552,9 @@ glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every, long l
         if (chunk > check_every) chunk = check_every;
         const bool last_chunk = done + chunk == n;
         const bool reduce_here = test || last_chunk || adapt;
-        for (long long s = 0; s < chunk; ++s) {
-            glbm_status st = do_step(h, reduce_here && s == chunk - 1);
-            if (st) return st;
-        }
+        if (glbm_status st = run_chunk(h, chunk, reduce_here, test ? tol : 0.0)) return st;
         done += chunk;
         h->steps += chunk;
-        if (reduce_here) finalize(h, test ? tol : 0.0);
         if (glbm_status st = launch_error(h)) return st;
         if (test || adapt) {
             if (glbm_status st = read_status(h)) return st;

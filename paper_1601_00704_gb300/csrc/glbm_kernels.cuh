@@ -284,9 +284,33 @@ __device__ __forceinline__ void collide_pair(R &gi, R &gj, R w, R wd, R eu, R eF
     }
 }
 
+// Error-free sum of g[first..8] as hi + lo (Knuth's TwoSum per addition,
+// explicitly rounded so nothing is reassociated or contracted).
+template <typename R>
+__device__ __forceinline__ void exact_sum(const R (&g)[9], int first, R &hi, R &lo) {
+    hi = g[first];
+    lo = R(0);
+#pragma unroll
+    for (int i = first + 1; i < 9; ++i) {
+        const R s = radd(hi, g[i]);
+        const R z = rsub(s, hi);
+        const R e = radd(rsub(hi, rsub(s, z)), rsub(g[i], z));
+        hi = s;
+        lo = radd(lo, e);
+    }
+}
+
 template <typename R, bool FORCH, bool CARRIER = true>
 __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
                                         const Phys<R> &ph, R &ux, R &uy) {
+    // Mass closure (CARRIER): the collision conserves each node's mass exactly
+    // in arithmetic, but rounding the nine stored populations does not, and
+    // the slow pressure mode integrates that per-node error over thousands of
+    // steps.  The exact sum of the streamed populations is kept, and the rest
+    // population is stored as the exact remainder after the eight moving ones
+    // (one rounding per node instead of nine).
+    R in_hi = R(0), in_lo = R(0);
+    if (CARRIER) exact_sum<R>(g, 0, in_hi, in_lo);
     R drho;
     node_velocity<R, FORCH>(g, alpha, eps, beta, ph, drho, ux, uy);
     const R rho = R(1) + drho;
@@ -314,6 +338,11 @@ __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
     collide_pair<R, CARRIER>(g[2], g[4], w1, wd1, uy, Fy, k1, om, su, a2, rho3, fb, f3, f9);
     collide_pair<R, CARRIER>(g[5], g[7], w2, wd2, ux + uy, Fx + Fy, k1, om, su, a2, rho3, fb, f3, f9);
     collide_pair<R, CARRIER>(g[6], g[8], w2, wd2, uy - ux, Fy - Fx, k1, om, su, a2, rho3, fb, f3, f9);
+    if (CARRIER) {
+        R out_hi, out_lo;
+        exact_sum<R>(g, 1, out_hi, out_lo);
+        g[0] = radd(rsub(in_hi, out_hi), rsub(in_lo, out_lo));
+    }
 }
 
 // ---------------------------------------------------------------------------

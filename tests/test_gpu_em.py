@@ -16,7 +16,19 @@ def pkg():
     return p
 
 
-@pytest.mark.parametrize("m,k", [(1, 1), (777, 2), (100003, 2), (50000, 3)])
+def test_em_single_sample_collapses(pkg, orc):
+    """One sample: the first iteration puts mu on it with zero variance (the
+    sample moments); the next E-step is undefined, reported as ENAN."""
+    x = np.array([3.25])
+    a = pkg.em_gmm1d(x, [1.0], [0.0], [1.0], max_iter=1, tol=0.0)
+    b = orc.em_gmm1d(x, [1.0], [0.0], [1.0], max_iter=1, tol=0.0)
+    assert a[1][0] == b[1][0] == 3.25 and a[2][0] == b[2][0] == 0.0 and a[0][0] == 1.0
+    with pytest.raises(pkg.GLBMError) as e:
+        pkg.em_gmm1d(x, [1.0], [0.0], [1.0], max_iter=3, tol=0.0)
+    assert e.value.name == "GLBM_ENAN"
+
+
+@pytest.mark.parametrize("m,k", [(2, 1), (777, 2), (100003, 2), (50000, 3)])
 def test_em_matches_oracle(pkg, orc, m, k):
     rng = np.random.default_rng(m + k)
     comps = [(10.0, 1.0, 0.25), (20.0, 4.0, 0.5), (35.0, 2.0, 0.25)][:k]
