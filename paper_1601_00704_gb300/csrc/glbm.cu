@@ -465,7 +465,7 @@ glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K, double
     CU(h, cudaMemsetAsync(h->buf[0], 0, size_t(9) * h->plane * h->elem, h->stream));
     CU(h, cudaMemsetAsync(h->buf[1], 0, size_t(9) * h->plane * h->elem, h->stream));
     if (glbm_status s = reset_status(h)) return s;
-    drop_graphs(h);  // the Forchheimer switch may change the kernel
+    if (h->forch != (F_eps != 0.0)) drop_graphs(h);  // another kernel instantiation
     h->cur = 0;
     h->steps = 0;
     h->tstep = 0;
