@@ -52,8 +52,9 @@ struct StepClock {
     unsigned int pad;
 };
 
+// Resident blocks as for k_step, scaled from its 128-thread blocks.
 template <typename T, int THREADS, bool WALLS, bool REDUCE>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, kMinBlocks<T> * 128 / THREADS)
 k_batch_step(const T *__restrict__ src_all, T *__restrict__ dst_all,
              const typename Store<T>::R *__restrict__ alpha, const typename Store<T>::R *__restrict__ epsv,
              const BTile *__restrict__ tiles, const BMed *__restrict__ meds, Phys<typename Store<T>::R> ph,

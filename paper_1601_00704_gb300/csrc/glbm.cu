@@ -130,7 +130,7 @@ glbm_status launch_step_t(glbm *h, bool reduce) {
     const R *a = static_cast<const R *>(h->coef[0]);
     const R *e = static_cast<const R *>(h->coef[1]);
     const R *b = static_cast<const R *>(h->coef[2]);
-    const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
+    const dim3 grid = step_grid(geo);
     if (reduce)
         k_step<T, VEC, WALLS, FORCH, true>
             <<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial, h->pmax);
@@ -725,8 +725,7 @@ glbm_status noalloc_scratch(double **out) {
 template <int VEC, bool WALLS, bool FORCH>
 void noalloc_launch(const float *src, float *dst, const float *a, const float *e, const float *b, const Geo &geo,
                     const Phys<float> &ph, double *partial, cudaStream_t st) {
-    const unsigned grid = unsigned(geo.bpr) * unsigned(geo.ny);
-    k_step<float, VEC, WALLS, FORCH, true><<<grid, kThreads, 0, st>>>(src, dst, a, e, b, geo, ph, partial, nullptr);
+    k_step<float, VEC, WALLS, FORCH, true><<<step_grid(geo), kThreads, 0, st>>>(src, dst, a, e, b, geo, ph, partial, nullptr);
 }
 
 }  // namespace

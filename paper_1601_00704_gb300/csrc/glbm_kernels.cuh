@@ -41,6 +41,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 namespace {
 
@@ -82,7 +83,11 @@ __device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a,
 __device__ __forceinline__ double rsqrt_(double a) { return __dsqrt_rn(a); }
 // Reciprocals of rho ~ 1, 2*c0 >= 1 and eps in (0, 1]: the hardware
 // approximation (within 1 ulp) is ample and a fraction of IEEE rcp's cost.
-__device__ __forceinline__ float rrcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ float rrcp(float a) {
+    float r;  // hardware approximate reciprocal (within 1 ulp); every argument here is >= 1/2
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double rrcp(double a) { return __drcp_rn(a); }
 
 // ---------------------------------------------------------------------------
@@ -265,23 +270,15 @@ __device__ __forceinline__ void node_velocity(const R (&g)[9], R alpha, R eps, R
 // Opposite directions share the even part of f_eq and F_i (terms in 1,
 // (e.u)^2, (e.u)(e.F)) and flip the odd part (e.u, e.F).  g[] holds the
 // streamed deviations on entry and the post-collision deviations on exit.
-template <typename R, bool CARRIER>
+template <typename R>
 __device__ __forceinline__ void collide_pair(R &gi, R &gj, R w, R wd, R eu, R eF, R k1, R om, R su, R a2,
                                              R rho3, R fb, R f3, R f9) {
     // even:  om [rho (9/(2 eps)(e.u)^2 - 3/(2 eps) u^2)] + rho A [9/eps (e.u)(e.F) - 3/eps u.F]
     // odd :  om [3 rho e.u] + rho A [3 e.F]
     const R ev = om * (a2 * eu * eu - su) + (fb + f9 * eu * eF);
     const R od = om * rho3 * eu + f3 * eF;
-    if (CARRIER) {
-        gi = wd + (k1 * (gi - wd) + w * (ev + od));
-        gj = wd + (k1 * (gj - wd) + w * (ev - od));
-    } else {
-        // 16-bit storage: its own rounding dominates, use the shorter form
-        // k1 g + om w d + w (even +- odd)
-        const R b = om * wd;
-        gi = k1 * gi + (b + w * (ev + od));
-        gj = k1 * gj + (b + w * (ev - od));
-    }
+    gi = wd + (k1 * (gi - wd) + w * (ev + od));
+    gj = wd + (k1 * (gj - wd) + w * (ev - od));
 }
 
 // Error-free sum of g[first..8] as hi + lo (Knuth's TwoSum per addition,
@@ -300,17 +297,17 @@ __device__ __forceinline__ void exact_sum(const R (&g)[9], int first, R &hi, R &
     }
 }
 
-template <typename R, bool FORCH, bool CARRIER = true>
+template <typename R, bool FORCH>
 __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
                                         const Phys<R> &ph, R &ux, R &uy) {
-    // Mass closure (CARRIER): the collision conserves each node's mass exactly
+    // Mass closure: the collision conserves each node's mass exactly
     // in arithmetic, but rounding the nine stored populations does not, and
     // the slow pressure mode integrates that per-node error over thousands of
     // steps.  The exact sum of the streamed populations is kept, and the rest
     // population is stored as the exact remainder after the eight moving ones
     // (one rounding per node instead of nine).
-    R in_hi = R(0), in_lo = R(0);
-    if (CARRIER) exact_sum<R>(g, 0, in_hi, in_lo);
+    R in_hi, in_lo;
+    exact_sum<R>(g, 0, in_hi, in_lo);
     R drho;
     node_velocity<R, FORCH>(g, alpha, eps, beta, ph, drho, ux, uy);
     const R rho = R(1) + drho;
@@ -332,41 +329,103 @@ __device__ __forceinline__ void collide(R (&g)[9], R alpha, R eps, R beta,
     const R fb = R(-3) * ie * rA * (ux * Fx + uy * Fy);
     const R w0 = wgt<R>(0), w1 = wgt<R>(1), w2 = wgt<R>(5);
     const R wd0 = w0 * drho, wd1 = w1 * drho, wd2 = w2 * drho;
-    if (CARRIER) g[0] = wd0 + (k1 * (g[0] - wd0) + w0 * (fb - om * su));
-    else g[0] = k1 * g[0] + (om * wd0 + w0 * (fb - om * su));
-    collide_pair<R, CARRIER>(g[1], g[3], w1, wd1, ux, Fx, k1, om, su, a2, rho3, fb, f3, f9);
-    collide_pair<R, CARRIER>(g[2], g[4], w1, wd1, uy, Fy, k1, om, su, a2, rho3, fb, f3, f9);
-    collide_pair<R, CARRIER>(g[5], g[7], w2, wd2, ux + uy, Fx + Fy, k1, om, su, a2, rho3, fb, f3, f9);
-    collide_pair<R, CARRIER>(g[6], g[8], w2, wd2, uy - ux, Fy - Fx, k1, om, su, a2, rho3, fb, f3, f9);
-    if (CARRIER) {
-        R out_hi, out_lo;
-        exact_sum<R>(g, 1, out_hi, out_lo);
-        g[0] = radd(rsub(in_hi, out_hi), rsub(in_lo, out_lo));
+    g[0] = wd0 + (k1 * (g[0] - wd0) + w0 * (fb - om * su));
+    collide_pair<R>(g[1], g[3], w1, wd1, ux, Fx, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R>(g[2], g[4], w1, wd1, uy, Fy, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R>(g[5], g[7], w2, wd2, ux + uy, Fx + Fy, k1, om, su, a2, rho3, fb, f3, f9);
+    collide_pair<R>(g[6], g[8], w2, wd2, uy - ux, Fy - Fx, k1, om, su, a2, rho3, fb, f3, f9);
+    R out_hi, out_lo;
+    exact_sum<R>(g, 1, out_hi, out_lo);
+    g[0] = radd(rsub(in_hi, out_hi), rsub(in_lo, out_lo));
+}
+
+// The same update for 16-bit storage, whose own rounding (2^-8 / 2^-11)
+// dwarfs any FP32 regrouping error: every population is k1 g + c_i with
+//   c_i = w_i [om (rho-1) + om rho (3 e.u + 9/(2 eps)(e.u)^2 - 3/(2 eps) u^2)
+//              + rho A (3 e.F + 9/eps (e.u)(e.F) - 3/eps u.F)],
+// folded per weight class into c = C + e.u (P e.u + Q e.F) +- (T e.u + U e.F)
+// (even part C + ..., odd part T e.u + U e.F); w_diagonal = w_axis / 4 and
+// w_0 = 4 w_axis, so the other classes are exact power-of-two multiples.
+template <typename R, bool FORCH>
+__device__ __forceinline__ void collide_small(R (&g)[9], R alpha, R eps, R beta,
+                                              const Phys<R> &ph, R &ux, R &uy) {
+    R drho;
+    node_velocity<R, FORCH>(g, alpha, eps, beta, ph, drho, ux, uy);
+    const R rho = R(1) + drho;
+    R Fx = eps * ph.gx - alpha * ux;
+    R Fy = eps * ph.gy - alpha * uy;
+    if (FORCH) {
+        const R bu = beta * sqrt(ux * ux + uy * uy);
+        Fx -= bu * ux;
+        Fy -= bu * uy;
     }
+    const R om = ph.omega, k1 = R(1) - om;
+    const R w1 = R(1.0 / 9.0);
+    const R cA = R(3) * w1 * ph.A;    // 3 w A
+    const R cO = R(1.5) * w1 * om;    // (3/2) w om
+    const R ier = rrcp(eps) * rho;    // rho / eps
+    const R uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+    const R C1 = (w1 * om) * drho - ier * (cA * uF + cO * uu);
+    const R P1 = (R(3) * cO) * ier, Q1 = (R(3) * cA) * ier;
+    const R T1 = (R(2) * cO) * rho, U1 = cA * rho;
+    g[0] = k1 * g[0] + R(4) * C1;
+    auto pair = [&](R &gi, R &gj, R eu, R eF, R s) {
+        const R E = s * (C1 + eu * (P1 * eu + Q1 * eF));
+        const R O = s * (T1 * eu + U1 * eF);
+        gi = k1 * gi + (E + O);
+        gj = k1 * gj + (E - O);
+    };
+    pair(g[1], g[3], ux, Fx, R(1));
+    pair(g[2], g[4], uy, Fy, R(1));
+    pair(g[5], g[7], ux + uy, Fx + Fy, R(0.25));
+    pair(g[6], g[8], uy - ux, Fy - Fx, R(0.25));
+}
+
+// Per-node coefficients of VEC consecutive nodes.
+template <typename R, int VEC>
+__device__ __forceinline__ void load_coef(const R *__restrict__ p, R (&c)[VEC]) {
+    if constexpr (VEC == 1) c[0] = p[0];
+    else ld16<R, VEC>(p, c);
 }
 
 // ---------------------------------------------------------------------------
-// Pull-streaming gather of VEC consecutive nodes (x0..x0+VEC-1, row y).
-// Phase 1 issues every load of the thread (9 vectors + up to 6 edge scalars)
-// before phase 2 consumes any, so all of them are in flight together.
+// Pull-streaming gather of VEC consecutive nodes (x0..x0+VEC-1, row y) and
+// of their coefficients (alpha, eps and, with Forchheimer, beta at node n0).
+// Phase 1 issues every load of the thread (9 vectors + up to 6 edge scalars +
+// 2-3 coefficient vectors) before phase 2 consumes any, so all of them are in
+// flight together.
 // ---------------------------------------------------------------------------
-template <typename T, int VEC, bool WALLS>
+// INTERIOR: 0 < y < ny-1, so no population crosses a wall or the periodic
+// y boundary and every shift mode is a compile-time constant.  x0 must be a
+// valid node (callers clamp idle threads to x0 = 0 and discard their result).
+template <typename T, int VEC, bool WALLS, bool INTERIOR, bool FORCH>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo, int x0, int y,
-                                       bool active, int lane, typename Store<T>::R inv_s,
-                                       typename Store<T>::R (&g)[VEC][9]) {
+                                       int lane, typename Store<T>::R inv_s,
+                                       const typename Store<T>::R *__restrict__ alpha,
+                                       const typename Store<T>::R *__restrict__ epsv,
+                                       const typename Store<T>::R *__restrict__ betav, long long n0,
+                                       typename Store<T>::R (&g)[VEC][9], typename Store<T>::R (&a)[VEC],
+                                       typename Store<T>::R (&e)[VEC], typename Store<T>::R (&b)[VEC]) {
     using R = typename Store<T>::R;
     const int nx = geo.nx, ny = geo.ny;
+    load_coef<R, VEC>(alpha + n0, a);
+    load_coef<R, VEC>(epsv + n0, e);
+    if (FORCH) load_coef<R, VEC>(betav + n0, b);
+    else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) b[k] = R(0);
+    }
     if constexpr (VEC == 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             int ys = y - cy(i);
             const T *p;
-            if (ys < 0 || ys >= ny) {
+            if (!INTERIOR && (ys < 0 || ys >= ny)) {
                 if (WALLS) {
                     // halfway bounce-back: the opposite population that left
                     // this node towards the wall returns reversed
                     p = src + (long long)opp(i) * geo.plane + (long long)y * nx + x0;
-                    g[0][i] = active ? Store<T>::ld(*p, inv_s) : R(0);
+                    g[0][i] = Store<T>::ld(*p, inv_s);
                     continue;
                 }
                 ys = ys < 0 ? ys + ny : ys - ny;
@@ -374,7 +433,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
             int xs = x0 - cx(i);
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             p = src + (long long)i * geo.plane + (long long)ys * nx + xs;
-            g[0][i] = active ? Store<T>::ld(*p, inv_s) : R(0);
+            g[0][i] = Store<T>::ld(*p, inv_s);
         }
     } else {
         // shift mode per population: 0 none, +1 take x-1, -1 take x+1;
@@ -391,7 +450,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
             int ys = y - cy(i);
             int pl = i;
             mode[i] = cx(i);
-            if (ys < 0 || ys >= ny) {
+            if (!INTERIOR && (ys < 0 || ys >= ny)) {
                 if (WALLS) {
                     pl = opp(i);
                     ys = y;
@@ -401,14 +460,10 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
                 }
             }
             const T *row = src + (long long)pl * geo.plane + (long long)ys * nx;
-            if (active) ld16<T, VEC>(row + x0, v[i]);
-            else {
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) v[i][k] = T(0);
-            }
+            ld16<T, VEC>(row + x0, v[i]);
             edge[i] = T(0);
-            if (mode[i] == 1 && active && first) edge[i] = row[xl];
-            if (mode[i] == -1 && active && last) edge[i] = row[xr];
+            if (mode[i] == 1 && first) edge[i] = row[xl];
+            if (mode[i] == -1 && last) edge[i] = row[xr];
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -437,17 +492,6 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
     }
 }
 
-template <typename R, int VEC>
-__device__ __forceinline__ void load_coef(const R *__restrict__ p, bool active, R (&c)[VEC]) {
-    if constexpr (VEC == 1) {
-        c[0] = active ? p[0] : R(1);
-    } else if (active) {
-        ld16<R, VEC>(p, c);
-    } else {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) c[k] = R(1);
-    }
-}
 
 // Deterministic block sum of two doubles; thread 0 returns the totals.
 __device__ __forceinline__ void block_sum2(double &a, double &b) {
@@ -501,24 +545,21 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
                                           double &sy, float &gm) {
     using R = typename Store<T>::R;
     const bool active = x0 < geo.nx;
+    x0 = active ? x0 : 0;  // idle threads read node 0 of the row and store nothing
     const int lane = threadIdx.x & 31;
     const long long n0 = (long long)y * geo.nx + x0;
 
-    R g[VEC][9];
-    gather<T, VEC, WALLS>(src, geo, x0, y, active, lane, ph.inv_scale, g);
-    R a[VEC], e[VEC], b[VEC];
-    load_coef<R, VEC>(alpha + n0, active, a);
-    load_coef<R, VEC>(epsv + n0, active, e);
-    if (FORCH) load_coef<R, VEC>(betav + n0, active, b);
-    else {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) b[k] = R(0);
-    }
+    R g[VEC][9], a[VEC], e[VEC], b[VEC];
+    if (y > 0 && y < geo.ny - 1)
+        gather<T, VEC, WALLS, true, FORCH>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e, b);
+    else
+        gather<T, VEC, WALLS, false, FORCH>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e, b);
 
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         R ux, uy;
-        collide<R, FORCH, !Store<T>::kSmall>(g[k], a[k], e[k], b[k], ph, ux, uy);
+        if constexpr (Store<T>::kSmall) collide_small<R, FORCH>(g[k], a[k], e[k], b[k], ph, ux, uy);
+        else collide<R, FORCH>(g[k], a[k], e[k], b[k], ph, ux, uy);
         if (REDUCE && active) {
             sx += double(ux);
             sy += double(uy);
@@ -528,8 +569,10 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
     if constexpr (Store<T>::kSmall && VEC == 4) {
         if (active && ph.sr) {
             // 16-bit storage, 4 nodes: two hardware stochastic-rounding
-            // conversions per population; the random words come from one
-            // hash per thread, stepped by a multiply-add and xor-folded
+            // conversions per population.  The random words are successive
+            // states of a full-period LCG seeded by one hash per thread; each
+            // state is a bijective image of the seed, hence uniform like it,
+            // which is all that unbiased rounding needs.
             uint32_t x = mix32(uint32_t(n0) ^ ph.step_key);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -539,9 +582,9 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
                 if (REDUCE)
                     gm = fmaxf(gm, fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3]))));
                 x = x * 0x2C1B3C6Du + 0x297A2D39u;
-                const uint32_t r0 = x ^ (x >> 15);
+                const uint32_t r0 = x;
                 x = x * 0x2C1B3C6Du + 0x297A2D39u;
-                const uint32_t r1 = x ^ (x >> 15);
+                const uint32_t r1 = x;
                 uint2 u;
                 u.x = Store<T>::pack_sr(v[0], v[1], r0);
                 u.y = Store<T>::pack_sr(v[2], v[3], r1);
@@ -587,26 +630,40 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
 // writes this block's FP64 sums of u_x, u_y to partial[2*block] and, for
 // 16-bit storage, the largest stored magnitude |g*S| to pmax[block].
 // ---------------------------------------------------------------------------
+// Grid: x = blocks of a row (geo.bpr), row y = blockIdx.y + kMaxGridY *
+// blockIdx.z (step_grid).  Blocks of 128 threads resident per SM, fixed by
+// measurement on GB300: FP32 and FP16 fit 64 registers (8 blocks, 32 warps);
+// BF16 spills at 64 and runs faster at 72 (7 blocks); FP64 is left free.
+constexpr int kMaxGridY = 65535;
+inline dim3 step_grid(const Geo &g) {
+    const int gy = g.ny < kMaxGridY ? g.ny : kMaxGridY;
+    return dim3(unsigned(g.bpr), unsigned(gy), unsigned((g.ny + kMaxGridY - 1) / kMaxGridY));
+}
+template <typename T>
+constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (std::is_same<T, __nv_bfloat16>::value ? 7 : 8);
+
 template <typename T, int VEC, bool WALLS, bool FORCH, bool REDUCE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::R *__restrict__ alpha,
        const typename Store<T>::R *__restrict__ epsv, const typename Store<T>::R *__restrict__ betav,
        Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ partial, float *__restrict__ pmax) {
-    const int y = blockIdx.x / geo.bpr;
-    const int bx = blockIdx.x - y * geo.bpr;
+    const int y = int(blockIdx.y) + kMaxGridY * int(blockIdx.z);
+    if (y >= geo.ny) return;  // padding of the last z slice (whole block)
+    const int bx = int(blockIdx.x);
     const int x0 = (bx * kThreads + threadIdx.x) * VEC;
+    const long long blk = (long long)y * geo.bpr + bx;  // reduction slot, row-major
     double sx = 0.0, sy = 0.0;
     float gm = 0.0f;
     step_body<T, VEC, WALLS, FORCH, REDUCE>(src, dst, alpha, epsv, betav, geo, ph, x0, y, sx, sy, gm);
     if (REDUCE) {
         block_sum2(sx, sy);
         if (threadIdx.x == 0) {
-            partial[2ll * blockIdx.x] = sx;
-            partial[2ll * blockIdx.x + 1] = sy;
+            partial[2 * blk] = sx;
+            partial[2 * blk + 1] = sy;
         }
         if constexpr (Store<T>::kSmall) {
             gm = block_max(gm);
-            if (threadIdx.x == 0) pmax[blockIdx.x] = gm;
+            if (threadIdx.x == 0) pmax[blk] = gm;
         }
     }
 }
@@ -768,10 +825,11 @@ k_velocity(const T *__restrict__ src, const typename Store<T>::R *__restrict__ a
     const bool active = x0 < geo.nx;
     if (!active) return;  // no shuffles on the scalar path
     const long long n = (long long)y * geo.nx + x0;
-    R g[1][9];
-    gather<T, 1, WALLS>(src, geo, x0, y, true, threadIdx.x & 31, ph.inv_scale, g);
+    R g[1][9], a[1], e[1], b[1];
+    gather<T, 1, WALLS, false, FORCH>(src, geo, x0, y, threadIdx.x & 31, ph.inv_scale, alpha, epsv, betav, n, g, a, e,
+                                      b);
     R drho, ux, uy;
-    node_velocity<R, FORCH>(g[0], alpha[n], epsv[n], FORCH ? betav[n] : R(0), ph, drho, ux, uy);
+    node_velocity<R, FORCH>(g[0], a[0], e[0], b[0], ph, drho, ux, uy);
     ux_out[n] = double(ux);
     uy_out[n] = double(uy);
     if (rho_out) rho_out[n] = 1.0 + double(drho);
