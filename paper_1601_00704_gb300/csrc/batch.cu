@@ -16,6 +16,7 @@
 
 #include "glbm.h"
 #include "glbm_kernels.cuh"
+#include "setup_kernels.cuh"
 
 #include <algorithm>
 #include <cmath>

@@ -17,6 +17,7 @@
 #include <new>
 
 #include "glbm_kernels.cuh"
+#include "setup_kernels.cuh"
 
 // ---------------------------------------------------------------------------
 // Host side.
