@@ -398,6 +398,50 @@ glbm_status glbm_nn_adam(float *p, const float *g, float *m, float *v,
                          long long count, float lr, float beta1, float beta2,
                          float eps, int t, void *stream);
 
+/* ===========================================================================
+ * Tensor-core inference of the same network (tcgen05, sm_103a).  Activations
+ * are NHWC BF16 device tensors whose pixel stride equals their channel count
+ * unless stated; weights are BF16 [ksize^2][cout][cin]; accumulation is FP32
+ * in tensor memory.  Like the FP32 kernels above this has no counterpart in
+ * the paper.  All calls enqueue on `stream`; EINVAL for bad sizes, NULL or
+ * misaligned pointers, ECUDA for a failed launch.
+ * ======================================================================== */
+
+/* y = conv(concat(x0, x1)) + bias, then max(., 0) when relu != 0; zero
+ * padding ksize/2 (ksize 1 or 3).  x0 holds c0 channels, x1 (may be NULL
+ * when c1 = 0) c1 channels of the same n x h x w images; c0 >= 32 and c1 are
+ * multiples of 32.  wt: BF16 [ksize^2][cout][c0 + c1]; bias: cout FP32;
+ * cout a multiple of 16 in [16, 256].  Output: f32_nchw = 0 -> BF16 NHWC at
+ * y with pixel stride ys >= cout (a multiple of 8; y may point at a channel
+ * slice of a wider tensor); f32_nchw != 0 -> the first cout_store channels
+ * as FP32 NCHW.  *err (device int, zeroed by the caller) receives a nonzero
+ * code if a pipeline wait in the kernel timed out (never in a correct run);
+ * the kernel then returns without hanging.  All pointers 16-byte aligned. */
+glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
+                            int n, int h, int w, int ksize, const void *wt,
+                            const float *bias, int cout, void *y,
+                            long long ys, int relu, int f32_nchw,
+                            int cout_store, int *err, void *stream);
+
+/* FP32 [cout][cin][ksize][ksize] -> BF16 [ksize^2][cout_pad][cin_pad] (the
+ * padding is zero). */
+glbm_status glbm_nn_tc_pack_weights(const float *w, int cout, int cin,
+                                    int ksize, int cout_pad, int cin_pad,
+                                    void *wt, void *stream);
+
+/* FP32 NCHW (n, c, h, w) -> BF16 NHWC with c_pad >= c channels (zero). */
+glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w,
+                                 void *y, int c_pad, void *stream);
+
+/* 2x2 average pool, BF16 NHWC (n, h, w, c) -> (n, h/2, w/2, c); c, h, w even. */
+glbm_status glbm_nn_pool2_nhwc(const void *x, int n, int c, int h, int w,
+                               void *y, void *stream);
+
+/* Nearest 2x upsample, BF16 NHWC (n, h, w, c) -> (n, 2h, 2w, c); c a
+ * multiple of 8. */
+glbm_status glbm_nn_upsample2_nhwc(const void *x, int n, int c, int h, int w,
+                                   void *y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

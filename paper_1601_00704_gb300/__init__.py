@@ -43,7 +43,9 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_batch_get_fields",
            "glbm_nn_conv_fwd", "glbm_nn_conv_bwd_data", "glbm_nn_conv_bwd_weight",
            "glbm_nn_relu_bwd", "glbm_nn_copy_channels", "glbm_nn_pool2",
-           "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam", "glbm_em_gmm1d"]
+           "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam", "glbm_em_gmm1d",
+           "glbm_nn_tc_conv", "glbm_nn_tc_pack_weights", "glbm_nn_nchw_to_nhwc",
+           "glbm_nn_pool2_nhwc", "glbm_nn_upsample2_nhwc"]
 
 
 class GLBMError(RuntimeError):
@@ -110,6 +112,11 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_nn_adam": ([_VP, _VP, _VP, _VP, ll, C.c_float, C.c_float, C.c_float,
                           C.c_float, i, _VP], i),
         "glbm_em_gmm1d": ([_VP, ll, i, _PD, _PD, _PD, i, d, C.POINTER(i), _PD, i, _VP], i),
+        "glbm_nn_tc_conv": ([_VP, i, _VP, i, i, i, i, i, _VP, _VP, i, _VP, ll, i, i, i, _VP, _VP], i),
+        "glbm_nn_tc_pack_weights": ([_VP, i, i, i, i, i, _VP, _VP], i),
+        "glbm_nn_nchw_to_nhwc": ([_VP, i, i, i, i, _VP, i, _VP], i),
+        "glbm_nn_pool2_nhwc": ([_VP, i, i, i, i, _VP, _VP], i),
+        "glbm_nn_upsample2_nhwc": ([_VP, i, i, i, i, _VP, _VP], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -8,7 +8,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu", "nn.cu", "em.cu")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu", "nn.cu", "nn_tc.cu", "em.cu")]
 HDR = [os.path.join(HERE, "csrc", n) for n in ("glbm_kernels.cuh", "setup_kernels.cuh")]
 OBJ = os.path.join(HERE, "csrc", "_obj")
 INCLUDE = os.path.join(ROOT, "include")

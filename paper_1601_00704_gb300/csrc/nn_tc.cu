@@ -1,0 +1,499 @@
+// Tensor-core (tcgen05) convolution for the warm-start network's inference
+// on GB300 (sm_103a), plus the NHWC layout kernels around it.
+//
+// The network (a U-Net of 3x3 convolutions) is the library's own addition;
+// the paper has no surrogate.  Its FP32 SIMT kernels (nn.cu) train it and
+// serve as the reference; this file runs the same forward pass on the 5th
+// generation tensor cores:
+//
+//  * activations NHWC in BF16 (pixel stride = the buffer's channel count);
+//    weights BF16 [tap][cout][cin]; FP32 accumulation in tensor memory;
+//  * implicit GEMM: M = 128 output pixels (a tw x th tile of one image),
+//    N = cout (16..256), K = taps x 32-channel chunks; per K step one TMA
+//    load of the shifted pixel tile (hardware zero fill outside the image is
+//    the convolution's zero padding) and one of the weight slice, both with
+//    the 64-byte swizzle that the MMA's shared-memory descriptors read;
+//  * the input channels may come from two tensors (c0 channels of x0, then
+//    c1 of x1): the decoder's skip concatenation is never materialised;
+//  * one CTA per output tile: warp 0 issues TMA, warp 1 issues tcgen05.mma
+//    into a TMEM accumulator, warps 2-5 read it back (tcgen05.ld), add the
+//    bias, apply ReLU and store BF16 NHWC (or FP32 NCHW for the head);
+//  * every wait on an mbarrier is bounded: on timeout the CTA records a
+//    code in *err, stops waiting, frees its TMEM and returns.
+
+#include "glbm.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+
+extern __attribute__((visibility("hidden"))) thread_local char g_create_err[512];
+
+namespace {
+
+constexpr int TC_M = 128;        // output pixels per tile (UMMA M)
+constexpr int TC_KC = 32;        // input channels per K step: 64-byte rows
+constexpr int TC_STAGES = 4;     // TMA ring depth
+constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
+constexpr int TC_STAGE_A = TC_M * TC_KC * 2;          // 8 KB
+constexpr long long kWaitCycles = 4ll << 30;          // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  Returns false (without
+// waiting further) once any thread of the CTA has given up.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+// ---- TMA --------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// ---- tcgen05 ----------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulator.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// The mbarrier receives one arrival when every MMA this thread issued so far
+// has completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Shared-memory matrix descriptor of a K-major tile whose rows are 64 bytes
+// (32 BF16) with the 64-byte swizzle, as TMA writes it: 8-row groups 512 B
+// apart (stride byte offset); the leading byte offset is unused for swizzled
+// K-major tiles; bits 46-47 hold the descriptor version 1; bits 61-63 the
+// swizzle mode (4 = 64 bytes).
+__device__ __forceinline__ uint64_t sdesc_k64(const void *tile) {
+    const uint64_t a = smem_u32(tile);
+    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((512ull >> 4) << 32) | (1ull << 46) | (4ull << 61);
+}
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N/8 in bits
+// 17-22, M/16 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(TC_M >> 4) << 24);
+}
+
+struct TcConvArgs {
+    int n, h, w, taps, nchunk0, nchunk, cout, tw, th;
+    uint32_t tmem_cols;
+    const float *bias;
+    void *y;
+    long long ys;  // output pixel stride (elements), NHWC output
+    int relu, f32_nchw, cout_store;
+    int *err;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+          const __grid_constant__ CUtensorMap mapB, const TcConvArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int stage_b = a.cout * TC_KC * 2;
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + TC_STAGES * TC_STAGE_A;
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * a.tw, y0 = blockIdx.y * a.th, img = blockIdx.z;
+    const int iters = a.taps * a.nchunk;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = uint32_t(a.tw * a.th * TC_KC * 2 + stage_b);
+            for (int i = 0; i < iters; ++i) {
+                const int s = i % TC_STAGES, use = i / TC_STAGES;
+                if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 1)) break;
+                const int tap = i / a.nchunk, ch = i - tap * a.nchunk;
+                const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+                mbar_expect_tx(&full[s], bytes);
+                if (ch < a.nchunk0)
+                    tma_load_4d(sA + s * TC_STAGE_A, &mapA0, &full[s], ch * TC_KC, x0 + dx, y0 + dy, img);
+                else
+                    tma_load_4d(sA + s * TC_STAGE_A, &mapA1, &full[s], (ch - a.nchunk0) * TC_KC, x0 + dx, y0 + dy,
+                                img);
+                tma_load_3d(sB + s * stage_b, &mapB, &full[s], ch * TC_KC, 0, tap);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(a.cout);
+            bool ok = true;
+            for (int i = 0; i < iters; ++i) {
+                const int s = i % TC_STAGES, use = i / TC_STAGES;
+                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 2)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sdesc_k64(sA + s * TC_STAGE_A), bd = sdesc_k64(sB + s * stage_b);
+#pragma unroll
+                for (int kk = 0; kk < TC_KC / 16; ++kk)  // K = 16 per MMA: 32 bytes along the row
+                    umma_bf16(tmem, ad + uint64_t((kk * 32) >> 4), bd + uint64_t((kk * 32) >> 4), idesc,
+                              (i > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(&empty[s]);
+            }
+            if (ok) umma_commit(&done);
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
+        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 3);
+        tc_fence_after();
+        if (have) {
+            const int m = q * 32 + lane;
+            const int px = x0 + m % a.tw, py = y0 + m / a.tw;
+            const bool ok = m < a.tw * a.th && px < a.w && py < a.h;
+            const long long pix = ((long long)img * a.h + py) * a.w + px;
+            for (int c = 0; c < a.cout; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(c), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] += a.bias[c + j];
+                    if (a.relu) v[j] = fmaxf(v[j], 0.0f);
+                }
+                if (!ok) continue;
+                if (a.f32_nchw) {
+                    float *yo = static_cast<float *>(a.y);
+                    const long long hw = (long long)a.h * a.w;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c + j < a.cout_store)
+                            yo[((long long)img * a.cout_store + c + j) * hw + (long long)py * a.w + px] = v[j];
+                } else {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        pk[j] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) + pix * a.ys + c);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+// ---- NHWC layout kernels (memory-bound, grid-stride) --------------------------
+__global__ void k_nchw_to_nhwc(const float *__restrict__ x, int n, int c, int h, int w,
+                               __nv_bfloat16 *__restrict__ y, int cp) {
+    const long long total = (long long)n * h * w * cp;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = int(i % cp);
+        const long long pix = i / cp;
+        const long long hw = (long long)h * w;
+        const long long img = pix / hw, p = pix - img * hw;
+        y[i] = __float2bfloat16_rn(ch < c ? x[(img * c + ch) * hw + p] : 0.0f);
+    }
+}
+
+// 2x2 average, FP32 arithmetic, two channels per thread.
+__global__ void k_pool2_nhwc(const __nv_bfloat162 *__restrict__ x, int n, int c2, int h, int w,
+                             __nv_bfloat162 *__restrict__ y) {
+    const int ho = h / 2, wo = w / 2;
+    const long long total = (long long)n * ho * wo * c2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = int(i % c2);
+        long long p = i / c2;
+        const int xo = int(p % wo);
+        p /= wo;
+        const int yo = int(p % ho);
+        const long long img = p / ho;
+        const long long base = ((img * h + 2 * yo) * w + 2 * xo) * c2 + ch;
+        const float2 a = __bfloat1622float2(x[base]), b = __bfloat1622float2(x[base + c2]);
+        const float2 d = __bfloat1622float2(x[base + (long long)w * c2]),
+                     e = __bfloat1622float2(x[base + (long long)w * c2 + c2]);
+        y[i] = __floats2bfloat162_rn(0.25f * ((a.x + b.x) + (d.x + e.x)), 0.25f * ((a.y + b.y) + (d.y + e.y)));
+    }
+}
+
+// Nearest 2x upsampling (h, w = input size), 16 bytes per thread.
+__global__ void k_up2_nhwc(const uint4 *__restrict__ x, int n, int c8, int h, int w, uint4 *__restrict__ y) {
+    const int ho = 2 * h, wo = 2 * w;
+    const long long total = (long long)n * ho * wo * c8;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ch = int(i % c8);
+        long long p = i / c8;
+        const int xo = int(p % wo);
+        p /= wo;
+        const int yo = int(p % ho);
+        const long long img = p / ho;
+        y[i] = x[((img * h + yo / 2) * w + xo / 2) * c8 + ch];
+    }
+}
+
+// FP32 [cout][cin][k][k] -> BF16 [k*k][cout_pad][cin_pad], zero padded.
+__global__ void k_pack_w_tc(const float *__restrict__ w, int cout, int cin, int k, int cout_pad, int cin_pad,
+                            __nv_bfloat16 *__restrict__ wt) {
+    const long long total = (long long)k * k * cout_pad * cin_pad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ci = int(i % cin_pad);
+        const int co = int((i / cin_pad) % cout_pad);
+        const int tap = int(i / ((long long)cin_pad * cout_pad));
+        float v = 0.0f;
+        if (ci < cin && co < cout) v = w[((long long)co * cin + ci) * k * k + tap];
+        wt[i] = __float2bfloat16_rn(v);
+    }
+}
+
+int grid_for(long long total) {
+    long long b = (total + 255) / 256;
+    return int(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+
+glbm_status tcfail(glbm_status s, const char *msg) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+    return s;
+}
+glbm_status tccuda(cudaError_t e, const char *what) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GLBM_ENOMEM : GLBM_ECUDA;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// NHWC BF16 activations: dims (channels, w, h, n), box (32, tw, th, 1).
+bool map_act(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int tw, int th) {
+    const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
+    const cuuint64_t strides[3] = {cuuint64_t(c) * 2, cuuint64_t(c) * 2 * w, cuuint64_t(c) * 2 * w * h};
+    const cuuint32_t box[4] = {TC_KC, cuuint32_t(tw), cuuint32_t(th), 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, int k,
+                                       const void *wt, const float *bias, int cout, void *y, long long ys, int relu,
+                                       int f32_nchw, int cout_store, int *err, void *stream) {
+    if (!x0 || !wt || !bias || !y || !err || (c1 > 0 && !x1))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: x0, wt, bias, y, err (and x1 when c1 > 0) are required");
+    if (n < 1 || h < 1 || w < 1 || (k != 1 && k != 3))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: need n, h, w >= 1 and k = 1 or 3");
+    if (c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: input channel counts must be multiples of 32 (c0 >= 32)");
+    if (cout < 16 || cout > 256 || cout % 16)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: cout must be a multiple of 16 in [16, 256]");
+    if (f32_nchw ? (cout_store < 1 || cout_store > cout) : (ys < cout || ys % 8))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: need 1 <= cout_store <= cout (FP32 NCHW output) or a pixel "
+                                   "stride ys >= cout, multiple of 8 (BF16 NHWC output)");
+    const uintptr_t mis = (uintptr_t(x0) | uintptr_t(x1) | uintptr_t(wt) | uintptr_t(y)) & 15u;
+    if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv: arrays must be 16-byte aligned");
+    if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv: cuTensorMapEncodeTiled is not available");
+    const int tw = w < TC_M ? w : TC_M;
+    const int th = TC_M / tw;
+    const long long gy = (h + th - 1) / th;
+    if (gy > 65535 || n > 65535) return tcfail(GLBM_EINVAL, "nn_tc_conv: image too tall or batch too large");
+
+    CUtensorMap mA0, mA1, mB;
+    if (!map_act(&mA0, x0, c0, w, h, n, tw, th) || !map_act(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, tw, th))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: activation tensor map rejected");
+    const int cin = c0 + c1, taps = k * k;
+    {
+        const cuuint64_t dims[3] = {cuuint64_t(cin), cuuint64_t(cout), cuuint64_t(taps)};
+        const cuuint64_t strides[2] = {cuuint64_t(cin) * 2, cuuint64_t(cin) * 2 * cout};
+        const cuuint32_t box[3] = {TC_KC, cuuint32_t(cout), 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (encode_fn()(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wt), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return tcfail(GLBM_EINVAL, "nn_tc_conv: weight tensor map rejected");
+    }
+    TcConvArgs a;
+    a.n = n;
+    a.h = h;
+    a.w = w;
+    a.taps = taps;
+    a.nchunk0 = c0 / TC_KC;
+    a.nchunk = cin / TC_KC;
+    a.cout = cout;
+    a.tw = tw;
+    a.th = th;
+    a.tmem_cols = 32;
+    while (a.tmem_cols < uint32_t(cout)) a.tmem_cols <<= 1;
+    a.bias = bias;
+    a.y = y;
+    a.ys = ys;
+    a.relu = relu ? 1 : 0;
+    a.f32_nchw = f32_nchw ? 1 : 0;
+    a.cout_store = f32_nchw ? cout_store : cout;
+    a.err = err;
+    const size_t smem = 1024 + size_t(TC_STAGES) * (TC_STAGE_A + size_t(cout) * TC_KC * 2);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute");
+    const dim3 grid(unsigned((w + tw - 1) / tw), unsigned(gy), unsigned(n));
+    k_tc_conv<<<grid, TC_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(mA0, mA1, mB, a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch");
+}
+
+extern "C" glbm_status glbm_nn_tc_pack_weights(const float *wf, int cout, int cin, int k, int cout_pad,
+                                               int cin_pad, void *wt, void *stream) {
+    if (!wf || !wt || cout < 1 || cin < 1 || (k != 1 && k != 3) || cout_pad < cout || cin_pad < cin)
+        return tcfail(GLBM_EINVAL, "nn_tc_pack_weights: invalid sizes or pointers");
+    const long long total = (long long)k * k * cout_pad * cin_pad;
+    k_pack_w_tc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        wf, cout, cin, k, cout_pad, cin_pad, static_cast<__nv_bfloat16 *>(wt));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_pack_weights launch");
+}
+
+extern "C" glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w, void *y, int c_pad,
+                                            void *stream) {
+    if (!x || !y || n < 1 || c < 1 || h < 1 || w < 1 || c_pad < c)
+        return tcfail(GLBM_EINVAL, "nn_nchw_to_nhwc: invalid sizes or pointers");
+    const long long total = (long long)n * h * w * c_pad;
+    k_nchw_to_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        x, n, c, h, w, static_cast<__nv_bfloat16 *>(y), c_pad);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_nchw_to_nhwc launch");
+}
+
+extern "C" glbm_status glbm_nn_pool2_nhwc(const void *x, int n, int c, int h, int w, void *y, void *stream) {
+    if (!x || !y || n < 1 || c < 2 || c % 2 || h < 2 || w < 2 || h % 2 || w % 2 ||
+        ((uintptr_t(x) | uintptr_t(y)) & 3u))
+        return tcfail(GLBM_EINVAL, "nn_pool2_nhwc: need even c, h, w and 4-byte aligned arrays");
+    const long long total = (long long)n * (h / 2) * (w / 2) * (c / 2);
+    k_pool2_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const __nv_bfloat162 *>(x), n, c / 2, h, w, static_cast<__nv_bfloat162 *>(y));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_pool2_nhwc launch");
+}
+
+extern "C" glbm_status glbm_nn_upsample2_nhwc(const void *x, int n, int c, int h, int w, void *y, void *stream) {
+    if (!x || !y || n < 1 || c < 8 || c % 8 || h < 1 || w < 1 || ((uintptr_t(x) | uintptr_t(y)) & 15u))
+        return tcfail(GLBM_EINVAL, "nn_upsample2_nhwc: need c a multiple of 8 and 16-byte aligned arrays");
+    const long long total = (long long)n * (2 * h) * (2 * w) * (c / 8);
+    k_up2_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const uint4 *>(x), n, c / 8, h, w, static_cast<uint4 *>(y));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_upsample2_nhwc launch");
+}

@@ -14,7 +14,10 @@ this is the library's own addition.
 Every computation of the network runs in the library's CUDA kernels
 (``glbm_nn_*``): 3x3 / 1x1 convolutions (forward, backward-data,
 backward-weight), 2x2 average pooling, nearest upsampling, ReLU, weighted
-MSE and Adam.  PyTorch only provides device memory and the stream.
+MSE and Adam, in FP32 for training.  Inference can also run on the tensor
+cores (``forward_tc``: tcgen05 implicit-GEMM convolutions on BF16 NHWC
+activations, FP32 accumulation).  PyTorch only provides device memory and
+the stream.
 
 Normalisation (all inputs/targets dimensionless, O(1)):
   inputs   (eps - 0.05) / 0.05,  (log10 K + 2) / 2,  log10(|G|) + 6
@@ -77,6 +80,9 @@ class UNet:
         self.wscratch = torch.empty(max(co * ci * k * k for _, ci, co, k in self.specs),
                                     dtype=torch.float32, device=dev)
         self._bufs = {}
+        self._version = 0     # bumped whenever the parameters change
+        self._tc = None       # (version, packed BF16 weights, padded biases)
+        self._tc_bufs = {}
 
     # -- plumbing -----------------------------------------------------------
     def _stream(self):
@@ -264,6 +270,7 @@ class UNet:
 
     def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         self.t += 1
+        self._version += 1
         self._ok(self.lib.glbm_nn_adam(_ptr(self.params), _ptr(self.grads), _ptr(self.m), _ptr(self.v),
                                        self.nparams, float(lr), float(beta1), float(beta2), float(eps), self.t,
                                        self._stream()), "adam")
@@ -279,6 +286,108 @@ class UNet:
         if p.size != self.nparams:
             raise ValueError(f"{path}: {p.size} parameters, this network has {self.nparams}")
         self.params.copy_(self.torch.from_numpy(p).cuda())
+        self._version += 1
+
+    def invalidate_tc(self):
+        """Call after writing ``params`` directly: the tensor-core path
+        repacks its BF16 weights on the next ``forward_tc``."""
+        self._version += 1
+
+    # -- tensor-core inference ------------------------------------------------
+    @staticmethod
+    def _pad(c, m):
+        return (c + m - 1) // m * m
+
+    def _tc_pack(self):
+        if self._tc is not None and self._tc[0] == self._version:
+            return self._tc
+        torch = self.torch
+        W, Bs = {}, {}
+        for name, ci, co, k in self.specs:
+            cip = max(32, self._pad(ci, 32))
+            cop = self._pad(co, 16)
+            wt = torch.empty(k * k * cop * cip, dtype=torch.bfloat16, device="cuda")
+            ow, ob = self._wb(name)
+            self._ok(self.lib.glbm_nn_tc_pack_weights(_ptr(self.params, ow), co, ci, k, cop, cip,
+                                                      C.c_void_p(wt.data_ptr()), self._stream()), "tc_pack")
+            b = torch.zeros(cop, dtype=torch.float32, device="cuda")
+            b[:co] = self.params[ob:ob + co]
+            W[name], Bs[name] = wt, b
+        self._tc = (self._version, W, Bs)
+        return self._tc
+
+    def _tc_buffers(self, n, h, w):
+        key = (n, h, w)
+        if key in self._tc_bufs:
+            return self._tc_bufs[key]
+        if h % 2 ** (self.levels - 1) or w % 2 ** (self.levels - 1):
+            raise ValueError(f"h, w must be multiples of {2 ** (self.levels - 1)}")
+        torch = self.torch
+
+        def z(c, l):
+            return torch.empty((n, h >> l, w >> l, c), dtype=torch.bfloat16, device="cuda")
+        B = {"x": z(max(32, self._pad(self.in_ch, 32)), 0)}
+        L = self.levels
+        for l in range(L):
+            c = self.ch[l]
+            B[f"a{l}"], B[f"e{l}"] = z(c, l), z(c, l)
+            if l < L - 1:
+                B[f"p{l}"] = z(c, l + 1)
+                B[f"u{l}"] = z(self.ch[l + 1], l)
+                B[f"da{l}"], B[f"d{l}"] = z(c, l), z(c, l)
+        B["y"] = torch.empty((n, self.out_ch, h, w), dtype=torch.float32, device="cuda")
+        B["err"] = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self._tc_bufs = {key: B}
+        return B
+
+    def _tc_conv(self, B, x0, c0, x1, c1, n, h, w, name, relu, y, head=False):
+        _, W, Bs = self._tc
+        k = 1 if head else 3
+        cop = Bs[name].numel()
+        self._ok(self.lib.glbm_nn_tc_conv(
+            C.c_void_p(x0.data_ptr()), c0, C.c_void_p(x1.data_ptr()) if x1 is not None else None, c1,
+            n, h, w, k, C.c_void_p(W[name].data_ptr()), C.c_void_p(Bs[name].data_ptr()), cop,
+            C.c_void_p(y.data_ptr()), cop, int(relu), int(head), self.out_ch if head else 0,
+            C.c_void_p(B["err"].data_ptr()), self._stream()), "tc_conv")
+
+    def forward_tc(self, x):
+        """The forward pass on the tensor cores: x (n, in_ch, h, w) FP32 CUDA
+        tensor -> (n, out_ch, h, w) FP32.  Activations are BF16 NHWC between
+        layers, accumulation FP32; the pipeline's error flag is checked."""
+        n, _, h, w = x.shape
+        self._tc_pack()
+        B = self._tc_buffers(n, h, w)
+        st = self._stream()
+        cin = B["x"].shape[3]
+        self._ok(self.lib.glbm_nn_nchw_to_nhwc(_ptr(x), n, self.in_ch, h, w, C.c_void_p(B["x"].data_ptr()),
+                                               cin, st), "nchw_to_nhwc")
+        L = self.levels
+        inp = B["x"]
+        for l in range(L):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            self._tc_conv(B, inp, cin, None, 0, n, hl, wl, f"e{l}a", True, B[f"a{l}"])
+            self._tc_conv(B, B[f"a{l}"], c, None, 0, n, hl, wl, f"e{l}b", True, B[f"e{l}"])
+            if l < L - 1:
+                self._ok(self.lib.glbm_nn_pool2_nhwc(C.c_void_p(B[f"e{l}"].data_ptr()), n, c, hl, wl,
+                                                     C.c_void_p(B[f"p{l}"].data_ptr()), st), "pool2_nhwc")
+                inp, cin = B[f"p{l}"], c
+        top, ctop = B[f"e{L - 1}"], self.ch[L - 1]
+        for l in range(L - 2, -1, -1):
+            hl, wl, c = h >> l, w >> l, self.ch[l]
+            self._ok(self.lib.glbm_nn_upsample2_nhwc(C.c_void_p(top.data_ptr()), n, ctop, hl // 2, wl // 2,
+                                                     C.c_void_p(B[f"u{l}"].data_ptr()), st), "upsample2_nhwc")
+            self._tc_conv(B, B[f"u{l}"], ctop, B[f"e{l}"], c, n, hl, wl, f"d{l}a", True, B[f"da{l}"])
+            self._tc_conv(B, B[f"da{l}"], c, None, 0, n, hl, wl, f"d{l}b", True, B[f"d{l}"])
+            top, ctop = B[f"d{l}"], c
+        self._tc_conv(B, top, ctop, None, 0, n, h, w, "head", False, B["y"], head=True)
+        return B["y"]
+
+    def tc_error(self):
+        """Nonzero if a tensor-core pipeline wait timed out since the buffers
+        were made (synchronises)."""
+        for B in self._tc_bufs.values():
+            return int(B["err"].item())
+        return 0
 
 
 # -- data --------------------------------------------------------------------

@@ -1,0 +1,181 @@
+"""Tensor-core (tcgen05) inference kernels of the warm-start network against
+the FP64 NumPy oracle (convolution on the same BF16-rounded inputs and
+weights) and against the FP32 network kernels (whole U-Net), through the C
+ABI.  BF16 NHWC activations, FP32 accumulation."""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import unet as ou
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1601_00704_gb300 import build
+    build.build()
+    import paper_1601_00704_gb300 as p
+    p.load()
+    return p
+
+
+def _bf16(a):
+    """Round to BF16 (nearest even) and back, on the host."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _vp(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# (n, h, w, c0, c1, cout, ksize, relu, f32 head output)
+CASES = [
+    (1, 16, 16, 32, 0, 32, 3, True, False),     # 2-D tile 16 x 8
+    (2, 20, 24, 64, 32, 48, 3, False, False),   # width not dividing 128, two input tensors
+    (1, 9, 200, 32, 0, 16, 3, True, False),     # wider than a tile, ragged in x and y
+    (1, 8, 8, 128, 128, 128, 3, True, False),   # smaller than one tile (rows beyond the image)
+    (2, 32, 40, 32, 0, 16, 1, False, True),     # 1x1 head, FP32 NCHW output of 3 channels
+    (1, 64, 256, 64, 0, 64, 3, True, False),    # several full 128-pixel tiles per row
+]
+
+
+@pytest.mark.parametrize("n,h,w,c0,c1,cout,k,relu,head", CASES)
+def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head):
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(hash((n, h, w, c0, c1, cout, k)) % 2 ** 32)
+    cin = c0 + c1
+    x = _bf16(rng.normal(size=(n, cin, h, w)))
+    wf = rng.normal(0.0, np.sqrt(2.0 / (cin * k * k)), size=(cout, cin, k, k)).astype(np.float32)
+    b = rng.normal(0.0, 0.1, size=cout).astype(np.float32)
+    ref = ou.conv(x, _bf16(wf), b.astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+
+    nhwc = torch.from_numpy(x.transpose(0, 2, 3, 1).astype(np.float32)).to(torch.bfloat16).cuda()
+    x0 = nhwc[..., :c0].contiguous()
+    x1 = nhwc[..., c0:].contiguous() if c1 else None
+    wt = torch.empty(k * k * cout * cin, dtype=torch.bfloat16, device="cuda")
+    wdev = torch.from_numpy(wf.ravel()).cuda()
+    assert lib.glbm_nn_tc_pack_weights(_vp(wdev), cout, cin, k, cout, cin, _vp(wt), _stream()) == 0
+    bdev = torch.from_numpy(b).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    store = 3 if head else 0
+    if head:
+        y = torch.full((n, store, h, w), float("nan"), dtype=torch.float32, device="cuda")
+    else:
+        y = torch.full((n, h, w, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+    rc = lib.glbm_nn_tc_conv(_vp(x0), c0, _vp(x1) if x1 is not None else None, c1, n, h, w, k, _vp(wt),
+                             _vp(bdev), cout, _vp(y), cout, int(relu), int(head), store, _vp(err), _stream())
+    assert rc == 0, pkg.load().glbm_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    scale = np.abs(ref).max()
+    if head:
+        got = y.cpu().numpy().astype(np.float64)
+        np.testing.assert_allclose(got, ref[:, :store], rtol=0, atol=2e-6 * scale)
+    else:
+        got = y.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
+        assert np.isfinite(got).all()
+        # the BF16 output rounding (half an ulp = 2^-9 relative) plus FP32 accumulation
+        bound = 2.0 ** -8 * np.abs(ref) + 1e-6 * scale
+        assert (np.abs(got - ref) <= bound).all(), np.abs(got - ref).max()
+
+
+def test_tc_conv_rejects_bad_shapes(pkg):
+    import torch
+    lib = pkg.load()
+    buf = torch.zeros(4096, dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(64, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def call(c0, cout, k):
+        return lib.glbm_nn_tc_conv(_vp(buf), c0, None, 0, 1, 4, 4, k, _vp(buf), _vp(b), cout, _vp(buf), cout,
+                                   1, 0, 0, _vp(err), _stream())
+    assert call(48, 32, 3) == -1   # input channels not a multiple of 32
+    assert b"multiples of 32" in lib.glbm_last_error(None)
+    assert call(32, 24, 3) == -1   # cout not a multiple of 16
+    assert b"cout" in lib.glbm_last_error(None)
+    assert call(32, 32, 5) == -1   # kernel size 5
+    assert b"k = 1 or 3" in lib.glbm_last_error(None)
+
+
+def test_nhwc_layout_kernels(pkg):
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(5)
+    n, c, h, w = 2, 5, 6, 10
+    x = rng.normal(size=(n, c, h, w)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty((n, h, w, 16), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_nchw_to_nhwc(_vp(xd), n, c, h, w, _vp(y), 16, _stream()) == 0
+    expect = np.zeros((n, h, w, 16), dtype=np.float32)
+    expect[..., :c] = x.transpose(0, 2, 3, 1)
+    exp_bf = torch.from_numpy(expect).to(torch.bfloat16)
+    assert torch.equal(y.cpu(), exp_bf)
+
+    # pool: FP32 sum (a + b) + (d + e), times 1/4, rounded to BF16
+    pooled = torch.empty((n, h // 2, w // 2, 16), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_pool2_nhwc(_vp(y), n, 16, h, w, _vp(pooled), _stream()) == 0
+    v = exp_bf.float().numpy()
+    s = (v[:, 0::2, 0::2] + v[:, 0::2, 1::2]) + (v[:, 1::2, 0::2] + v[:, 1::2, 1::2])
+    ref = torch.from_numpy((np.float32(0.25) * s).astype(np.float32)).to(torch.bfloat16)
+    assert torch.equal(pooled.cpu(), ref)
+
+    up = torch.empty((n, h, w, 16), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_upsample2_nhwc(_vp(pooled), n, 16, h // 2, w // 2, _vp(up), _stream()) == 0
+    ref_up = ref.repeat_interleave(2, dim=1).repeat_interleave(2, dim=2)
+    assert torch.equal(up.cpu(), ref_up)
+
+
+@pytest.mark.parametrize("levels,max_ch,size", [(3, 64, 32), (4, None, 64)])
+def test_unet_forward_tc_matches_fp32(pkg, levels, max_ch, size):
+    """Random-initialised network: the tensor-core forward pass agrees with the
+    FP32 kernels to the BF16 activation rounding accumulated over the layers."""
+    import torch
+    from paper_1601_00704_gb300.surrogate import UNet
+    net = UNet(base=32, levels=levels, seed=3, max_ch=max_ch)
+    rng = np.random.default_rng(11)
+    x = torch.from_numpy(rng.normal(size=(2, 3, size, size)).astype(np.float32)).cuda()
+    y32 = net.forward(x).clone()
+    ytc = net.forward_tc(x).clone()
+    torch.cuda.synchronize()
+    assert net.tc_error() == 0
+    rel = float((ytc - y32).norm() / y32.norm())
+    assert rel < 2e-2, rel
+
+
+def test_trained_network_tc_prediction(pkg):
+    """The committed network on an unseen medium of its training recipe: the
+    tensor-core prediction matches the FP32 one in every output channel."""
+    import json
+    import os
+
+    import torch
+
+    import media
+    from paper_1601_00704_gb300 import surrogate
+    from paper_1601_00704_gb300 import train_surrogate as T
+    meta = json.load(open(os.path.splitext(T.DEFAULT_WEIGHTS)[0] + ".json"))
+    net = surrogate.UNet(base=meta["base"], levels=meta["levels"], max_ch=meta.get("max_ch"))
+    net.load(T.DEFAULT_WEIGHTS)
+    m = media.shale_batch(1, seed=9101, sides=(256,))[0]
+    K = T.medium_k(pkg, m)
+    x = torch.from_numpy(surrogate.features(m["eps"], K, T.G)[None]).cuda()
+    y32 = net.forward(x).clone()
+    ytc = net.forward_tc(x).clone()
+    torch.cuda.synchronize()
+    assert net.tc_error() == 0
+    for ch in range(3):
+        rel = float((ytc[0, ch] - y32[0, ch]).norm() / y32[0, ch].norm())
+        print(f"channel {ch}: relative L2 difference {rel:.2e}")
+        assert rel < 3e-2, (ch, rel)
