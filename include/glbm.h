@@ -442,6 +442,21 @@ glbm_status glbm_nn_pool2_nhwc(const void *x, int n, int c, int h, int w,
 glbm_status glbm_nn_upsample2_nhwc(const void *x, int n, int c, int h, int w,
                                    void *y, void *stream);
 
+/* Warm-start input of one medium of npix nodes (FP64 eps and K on the
+ * device) -> x, 3 x npix FP32 (one NCHW sample): (eps - 0.05)/0.05,
+ * (log10 K + 2)/2 and log10|G| + 6. */
+glbm_status glbm_nn_warm_features(const double *eps, const double *K,
+                                  long long npix, double G, float *x,
+                                  void *stream);
+
+/* Network output y (3 x npix FP32) -> FP64 warm-start fields on the device:
+ * rho = 1 + y0 G rho_scale, ux = y1 K G / nu, uy = y2 K G / nu, ready for
+ * glbm_init_equilibrium with device_ptrs = 1. */
+glbm_status glbm_nn_warm_decode(const float *y, const double *K,
+                                long long npix, double G, double nu,
+                                double rho_scale, double *rho, double *ux,
+                                double *uy, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

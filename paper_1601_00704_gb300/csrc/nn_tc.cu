@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -346,6 +347,33 @@ __global__ void k_pack_w_tc(const float *__restrict__ w, int cout, int cin, int 
     }
 }
 
+// Network input of one medium (features of the warm start): channel 0
+// (eps - 0.05) / 0.05, channel 1 (log10 K + 2) / 2, channel 2 the constant
+// log10|G| + 6 (passed in), FP64 arithmetic rounded once to FP32.
+__global__ void k_warm_features(const double *__restrict__ eps, const double *__restrict__ K, long long np,
+                                float g6, float *__restrict__ x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        x[i] = float(__ddiv_rn(__dsub_rn(eps[i], 0.05), 0.05));
+        x[np + i] = float(__ddiv_rn(__dadd_rn(log10(K[i]), 2.0), 2.0));
+        x[2 * np + i] = g6;
+    }
+}
+
+// Network output -> warm-start fields: rho = 1 + y0 G s, u = y K G / nu
+// (the network predicts the density deviation over G s and the velocity over
+// the local Darcy scale K G / nu), FP64, rounded in the written order.
+__global__ void k_warm_decode(const float *__restrict__ y, const double *__restrict__ K, long long np, double G,
+                              double nu, double s, double *__restrict__ rho, double *__restrict__ ux,
+                              double *__restrict__ uy) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
+         i += (long long)gridDim.x * blockDim.x) {
+        rho[i] = __dadd_rn(1.0, __dmul_rn(__dmul_rn(double(y[i]), G), s));
+        ux[i] = __ddiv_rn(__dmul_rn(__dmul_rn(double(y[np + i]), K[i]), G), nu);
+        uy[i] = __ddiv_rn(__dmul_rn(__dmul_rn(double(y[2 * np + i]), K[i]), G), nu);
+    }
+}
+
 int grid_for(long long total) {
     long long b = (total + 255) / 256;
     return int(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
@@ -496,4 +524,24 @@ extern "C" glbm_status glbm_nn_upsample2_nhwc(const void *x, int n, int c, int h
         static_cast<const uint4 *>(x), n, c / 8, h, w, static_cast<uint4 *>(y));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_upsample2_nhwc launch");
+}
+
+extern "C" glbm_status glbm_nn_warm_features(const double *eps, const double *K, long long npix, double G, float *x,
+                                             void *stream) {
+    if (!eps || !K || !x || npix < 1 || !(G != 0.0) || !std::isfinite(G))
+        return tcfail(GLBM_EINVAL, "nn_warm_features: need eps, K, x, npix >= 1 and finite G != 0");
+    k_warm_features<<<grid_for(npix), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        eps, K, npix, float(log10(fabs(G)) + 6.0), x);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_warm_features launch");
+}
+
+extern "C" glbm_status glbm_nn_warm_decode(const float *y, const double *K, long long npix, double G, double nu,
+                                           double rho_scale, double *rho, double *ux, double *uy, void *stream) {
+    if (!y || !K || !rho || !ux || !uy || npix < 1 || !(nu > 0.0))
+        return tcfail(GLBM_EINVAL, "nn_warm_decode: need y, K, rho, ux, uy, npix >= 1 and nu > 0");
+    k_warm_decode<<<grid_for(npix), 256, 0, static_cast<cudaStream_t>(stream)>>>(y, K, npix, G, nu, rho_scale,
+                                                                                  rho, ux, uy);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_warm_decode launch");
 }

@@ -409,6 +409,24 @@ def targets(rho, ux, uy, K, G, nu):
     return t
 
 
+def predict_device(net, eps, K, G, nu, tc=True):
+    """Warm-start fields from FP64 CUDA tensors eps, K (ny, nx), computed on
+    the device end to end: features kernel, the network (tensor cores when
+    tc, else the FP32 kernels), decode kernel.  Returns FP64 CUDA tensors
+    (rho, ux, uy) for Solver.init_equilibrium."""
+    torch = net.torch
+    ny, nx = eps.shape
+    npix = ny * nx
+    st = net._stream()
+    x = torch.empty((1, 3, ny, nx), dtype=torch.float32, device="cuda")
+    net._ok(net.lib.glbm_nn_warm_features(_ptr(eps), _ptr(K), npix, float(G), _ptr(x), st), "warm_features")
+    y = net.forward_tc(x) if tc else net.forward(x)
+    out = [torch.empty((ny, nx), dtype=torch.float64, device="cuda") for _ in range(3)]
+    net._ok(net.lib.glbm_nn_warm_decode(_ptr(y), _ptr(K), npix, float(G), float(nu), RHO_SCALE,
+                                        *[_ptr(o) for o in out], st), "warm_decode")
+    return tuple(out)
+
+
 def decode(y, K, G, nu):
     """Network output (3, ny, nx) -> (rho, ux, uy) FP64."""
     y = np.asarray(y, dtype=np.float64)

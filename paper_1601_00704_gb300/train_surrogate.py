@@ -127,14 +127,14 @@ def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0)):
     return hist
 
 
-def predict(net, eps, K):
-    """Warm-start fields (rho, ux, uy) for one medium of any size (multiple
-    of 2^(levels-1))."""
+def predict(net, eps, K, tc=False):
+    """Warm-start fields (rho, ux, uy) as host arrays for one medium of any
+    size (multiple of 2^(levels-1)); tc runs the network on the tensor cores."""
     import torch
 
     from paper_1601_00704_gb300 import surrogate
     x = torch.from_numpy(surrogate.features(eps, K, G)[None]).cuda()
-    y = net.forward(x).cpu().numpy()[0]
+    y = (net.forward_tc(x) if tc else net.forward(x)).cpu().numpy()[0]
     return surrogate.decode(y, K, G, NU)
 
 
@@ -192,11 +192,13 @@ def main(argv=None):
 
 def time_to_k(pkg, eps, K, k_ref, storage="f32", init=None, check=1000, crit=1e-3, max_steps=3_000_000):
     """Steps and CUDA-event seconds until |K_app/k_ref - 1| <= crit, from rest
-    or from init = (rho, ux, uy) (the initialisation is inside the timing)."""
+    or from init = (rho, ux, uy) (the initialisation is inside the timing).
+    eps, K (and init) may be host arrays or FP64 CUDA tensors."""
     import torch
     stream = torch.cuda.Stream()
     n = eps.shape[0]
     s = pkg.Solver(eps.shape[1], n, tau=TAU, storage=storage, stream=stream)
+    torch.cuda.synchronize()
     s.set_medium(eps, K)
     s.set_force(G)
     torch.cuda.synchronize()
@@ -239,16 +241,28 @@ def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
     k_ref = ref.permeability()
     ref_s = time.perf_counter() - t0
     ref.close()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rho, ux, uy = predict(net, m["eps"], K)
-    torch.cuda.synchronize()
-    infer_s = time.perf_counter() - t0
-    k_raw = NU * float(np.mean(ux)) / G
-    runs = {"cold_f32": time_to_k(pkg, m["eps"], K, k_ref),
-            "warm_f32": time_to_k(pkg, m["eps"], K, k_ref, init=(rho, ux, uy)),
-            "cold_bf16": time_to_k(pkg, m["eps"], K, k_ref, storage="bf16"),
-            "warm_bf16": time_to_k(pkg, m["eps"], K, k_ref, storage="bf16", init=(rho, ux, uy))}
+    from paper_1601_00704_gb300 import surrogate
+    # the medium is uploaded once: the solver and the network both read it
+    eps_d = torch.from_numpy(np.ascontiguousarray(m["eps"], dtype=np.float64)).cuda()
+    K_d = torch.from_numpy(np.ascontiguousarray(K, dtype=np.float64)).cuda()
+
+    def infer(tc):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f = surrogate.predict_device(net, eps_d, K_d, G, NU, tc=tc)
+        torch.cuda.synchronize()
+        return f, time.perf_counter() - t0
+    infer(False)
+    infer(True)  # first calls allocate buffers and pack the BF16 weights
+    _, infer32_s = infer(False)
+    fields, infer_s = infer(True)
+    if net.tc_error():
+        raise RuntimeError("tensor-core pipeline reported a timeout")
+    k_raw = NU * float(fields[1].cpu().numpy().mean()) / G
+    runs = {"cold_f32": time_to_k(pkg, eps_d, K_d, k_ref),
+            "warm_f32": time_to_k(pkg, eps_d, K_d, k_ref, init=fields),
+            "cold_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16"),
+            "warm_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", init=fields)}
     for r in ("warm_f32", "warm_bf16"):
         runs[r]["seconds_with_inference"] = runs[r]["seconds"] + infer_s
     base = runs["cold_f32"]["seconds"]
@@ -256,7 +270,9 @@ def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
            "k_ref": k_ref, "k_ref_from": f"FP32 cold run to relative change < {ref_tol:g} per 1e4 steps "
                                          f"({ref_steps} steps, converged={conv}, {ref_s:.1f} s)",
            "criterion": "|K_app/K_ref - 1| <= 1e-3, checked every 1000 steps",
-           "surrogate_raw_k_app_rel_err": k_raw / k_ref - 1, "inference_s": infer_s, "runs": runs,
+           "surrogate_raw_k_app_rel_err": k_raw / k_ref - 1, "inference_s": infer_s,
+           "inference": "device-resident: features kernel, tensor-core (tcgen05) U-Net, decode kernel",
+           "inference_fp32_kernels_s": infer32_s, "runs": runs,
            "speedup_vs_cold_f32": {r: base / v.get("seconds_with_inference", v["seconds"])
                                    for r, v in runs.items() if v["met"] and r != "cold_f32"}}
     log(json.dumps(out))

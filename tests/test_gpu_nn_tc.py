@@ -179,3 +179,33 @@ def test_trained_network_tc_prediction(pkg):
         rel = float((ytc[0, ch] - y32[0, ch]).norm() / y32[0, ch].norm())
         print(f"channel {ch}: relative L2 difference {rel:.2e}")
         assert rel < 3e-2, (ch, rel)
+
+
+def test_device_features_and_decode_match_host(pkg):
+    """The device-resident warm-start plumbing computes what the host
+    definitions (surrogate.features / decode) compute: decode bit for bit,
+    features to one FP32 rounding (log10 may differ in the last FP64 bit)."""
+    import torch
+
+    import media
+    from paper_1601_00704_gb300 import surrogate
+    from paper_1601_00704_gb300 import train_surrogate as T
+    lib = pkg.load()
+    m = media.shale_batch(1, seed=9102, sides=(64,))[0]
+    K = T.medium_k(pkg, m)
+    eps_d = torch.from_numpy(np.ascontiguousarray(m["eps"], dtype=np.float64)).cuda()
+    K_d = torch.from_numpy(np.ascontiguousarray(K, dtype=np.float64)).cuda()
+    x = torch.empty((3, 64, 64), dtype=torch.float32, device="cuda")
+    assert lib.glbm_nn_warm_features(_vp(eps_d), _vp(K_d), 64 * 64, T.G, _vp(x), _stream()) == 0
+    ref = surrogate.features(m["eps"], K, T.G)
+    got = x.cpu().numpy()
+    np.testing.assert_allclose(got[:2], ref[:2], rtol=2.0 ** -23, atol=0)
+    np.testing.assert_allclose(got[2], ref[2], rtol=0, atol=1e-9)  # log10|G| + 6, host libm on both sides
+
+    y = np.random.default_rng(3).normal(size=(3, 64, 64)).astype(np.float32)
+    yd = torch.from_numpy(y).cuda()
+    out = [torch.empty((64, 64), dtype=torch.float64, device="cuda") for _ in range(3)]
+    assert lib.glbm_nn_warm_decode(_vp(yd), _vp(K_d), 64 * 64, T.G, T.NU, surrogate.RHO_SCALE,
+                                   *[_vp(o) for o in out], _stream()) == 0
+    for got, exp in zip(out, surrogate.decode(y, K, T.G, T.NU)):
+        assert np.array_equal(got.cpu().numpy(), exp)
