@@ -15,7 +15,9 @@
 //    the 64-byte swizzle that the MMA's shared-memory descriptors read;
 //  * the input channels may come from two tensors (c0 channels of x0, then
 //    c1 of x1): the decoder's skip concatenation is never materialised;
-//  * one CTA per output tile: warp 0 issues TMA, warp 1 issues tcgen05.mma
+//  * one CTA per output tile with a 3-stage TMA ring (short, so that 4-6
+//    CTAs share an SM and hide each other's latency): warp 0 issues TMA,
+//    warp 1 issues tcgen05.mma
 //    into a TMEM accumulator, warps 2-5 read it back (tcgen05.ld), add the
 //    bias, apply ReLU and store BF16 NHWC (or FP32 NCHW for the head);
 //  * every wait on an mbarrier is bounded: on timeout the CTA records a
@@ -38,7 +40,7 @@ namespace {
 
 constexpr int TC_M = 128;        // output pixels per tile (UMMA M)
 constexpr int TC_KC = 32;        // input channels per K step: 64-byte rows
-constexpr int TC_STAGES = 4;     // TMA ring depth
+constexpr int TC_STAGES = 3;     // TMA ring depth (2, 3, 4 and 7-8 measured: 3 best, occupancy wins)
 constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
 constexpr int TC_STAGE_A = TC_M * TC_KC * 2;          // 8 KB
 constexpr long long kWaitCycles = 4ll << 30;          // ~2 s at 2 GHz
@@ -173,8 +175,9 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int stage_b = a.cout * TC_KC * 2;
     uint8_t *sA = smem;
-    uint8_t *sB = smem + TC_STAGES * TC_STAGE_A;
-    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    constexpr int S = TC_STAGES;
+    uint8_t *sB = smem + S * TC_STAGE_A;
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
@@ -183,7 +186,7 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     const int iters = a.taps * a.nchunk;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -201,7 +204,7 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
         if (lane == 0) {
             const uint32_t bytes = uint32_t(a.tw * a.th * TC_KC * 2 + stage_b);
             for (int i = 0; i < iters; ++i) {
-                const int s = i % TC_STAGES, use = i / TC_STAGES;
+                const int s = i % S, use = i / S;
                 if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 1)) break;
                 const int tap = i / a.nchunk, ch = i - tap * a.nchunk;
                 const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
@@ -219,7 +222,7 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
             const uint32_t idesc = idesc_bf16(a.cout);
             bool ok = true;
             for (int i = 0; i < iters; ++i) {
-                const int s = i % TC_STAGES, use = i / TC_STAGES;
+                const int s = i % S, use = i / S;
                 if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 2)) {
                     ok = false;
                     break;

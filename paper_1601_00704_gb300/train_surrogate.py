@@ -158,10 +158,20 @@ def main(argv=None):
     p.add_argument("--out", default=DEFAULT_WEIGHTS)
     p.add_argument("--study", action="store_true", help="run the 2048^2 warm-start study after training")
     p.add_argument("--study-only", metavar="WEIGHTS", help="load these weights and only run the study")
+    p.add_argument("--infer", type=int, metavar="N",
+                   help="time device-resident inference of the committed (or --weights) network on one N x N "
+                        "medium of the training recipe, then exit")
+    p.add_argument("--weights", default=DEFAULT_WEIGHTS, help="weights for --infer")
+    p.add_argument("--fp32", action="store_true", help="--infer with the FP32 kernels instead of the tensor cores")
     a = p.parse_args(argv)
     from paper_1601_00704_gb300 import build
     build.build()
     from paper_1601_00704_gb300 import surrogate
+    if a.infer:
+        net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)
+        net.load(a.weights)
+        print(json.dumps(infer_timing(net, a.infer, tc=not a.fp32)))
+        return
     if a.study_only:
         net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)
         net.load(a.study_only)
@@ -220,6 +230,34 @@ def time_to_k(pkg, eps, K, k_ref, storage="f32", init=None, check=1000, crit=1e-
            "met": abs(k / k_ref - 1) <= crit}
     s.close()
     return out
+
+
+def infer_timing(net, n, seed=4242, reps=3, tc=True):
+    """CUDA-event time of one device-resident prediction (features kernel,
+    network, decode kernel) on an n x n medium of the training recipe, after
+    one warm-up pass that allocates buffers and packs weights."""
+    import torch
+
+    import media
+    import paper_1601_00704_gb300 as pkg
+    from paper_1601_00704_gb300 import surrogate
+    m = media.shale_batch(1, seed=seed, sides=(n,))[0]
+    K = medium_k(pkg, m)
+    eps_d = torch.from_numpy(np.ascontiguousarray(m["eps"], dtype=np.float64)).cuda()
+    K_d = torch.from_numpy(np.ascontiguousarray(K, dtype=np.float64)).cuda()
+    surrogate.predict_device(net, eps_d, K_d, G, NU, tc=tc)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        surrogate.predict_device(net, eps_d, K_d, G, NU, tc=tc)
+    e1.record()
+    e1.synchronize()
+    err = net.tc_error() if tc else 0
+    if err:
+        raise RuntimeError(f"tensor-core pipeline reported a timeout (code {err})")
+    return {"n": n, "path": "tensor cores (tcgen05, BF16)" if tc else "FP32 kernels",
+            "ms_per_prediction": e0.elapsed_time(e1) / reps}
 
 
 def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
