@@ -81,6 +81,9 @@ def args_():
                    help="skip the batched-media (DGM/GMS sweep) measurement")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-steps", type=int, default=500)
+    p.add_argument("--sweep", type=int, default=0, metavar="STEPS",
+                   help="also run the 25-cell medium sweep (OM fraction x correlation length at nx x ny), "
+                        "each cell up to STEPS time steps or converged (off by default: minutes)")
     return p.parse_args()
 
 
@@ -452,6 +455,50 @@ def batch_bench(a):
 
 # -- learned warm start ---------------------------------------------------------
 
+SWEEP_OM = (0.05, 0.10, 0.20, 0.30, 0.40)
+SWEEP_CORR = (4, 8, 16, 32, 64)
+
+
+def sweep(a):
+    """The two-phase workload over OM fraction x correlation length: per
+    cell the kernel throughput (CUDA events over the whole run) and K_app
+    after at most a.sweep steps or convergence (relative change of U_x
+    below 1e-10 per 1000 steps)."""
+    import torch
+
+    import media
+    import paper_1601_00704_gb300 as pkg
+    stream = torch.cuda.Stream()
+    cells = []
+    bytes_per = ELEM[a.storage] * 18 + 2 * (8 if a.storage == "f64" else 4)
+    peak = peaks()[0]
+    for om in SWEEP_OM:
+        for cl in SWEEP_CORR:
+            eps, K, _ = media.two_phase_medium(a.nx, a.ny, om_fraction=om, corr_len=cl, seed=a.seed)
+            s = pkg.Solver(a.nx, a.ny, tau=TAU, storage=a.storage, stream=stream)
+            s.set_medium(eps, K)
+            s.set_force(G)
+            s.step(100)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            done, conv = s.step(a.sweep, tol=1e-10, check_every=1000)
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) * 1e-3
+            glups = a.nx * a.ny * done / sec / 1e9
+            cells.append({"om_fraction": om, "corr_len": cl, "steps": done, "converged": bool(conv),
+                          "glups": glups, "frac_of_measured_hbm": glups * bytes_per / peak,
+                          "k_app": s.permeability()})
+            s.close()
+    g = [c["glups"] for c in cells]
+    return {"workload": f"{a.nx}x{a.ny} two-phase media, OM fraction {list(SWEEP_OM)} x correlation length "
+                        f"{list(SWEEP_CORR)}, seed {a.seed}, storage {a.storage}, up to {a.sweep} steps or "
+                        f"relative change of U_x < 1e-10 per 1000 steps",
+            "glups_min": min(g), "glups_max": max(g), "cells": cells}
+
+
 def warm_start(a):
     """Cold vs surrogate-initialised runs (FP32 and BF16) on an unseen 2048^2
     medium of the surrogate's training recipe, with the committed weights."""
@@ -589,7 +636,7 @@ def run_ours(a, world, rank, local):
     s.close()
     # single-GPU studies (skipped under torchrun, where only the scaling
     # measurement above is wanted)
-    ttp = batch = formats = warm = None
+    ttp = batch = formats = warm = swp = None
     if world == 1:
         formats = format_throughput(a, eps, K)
         if not a.no_ttp:
@@ -598,6 +645,8 @@ def run_ours(a, world, rank, local):
             warm = warm_start(a)
         if not a.no_batch:
             batch = batch_bench(a)
+        if a.sweep > 0:
+            swp = sweep(a)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -613,6 +662,8 @@ def run_ours(a, world, rank, local):
             "warm_start": warm,
             "batch": batch,
         }
+        if swp is not None:
+            line["sweep"] = swp
         print(json.dumps(line), flush=True)
     return 0
 
