@@ -429,7 +429,8 @@ glbm_status glbm_nn_tc_pack_weights(const float *w, int cout, int cin,
                                     int ksize, int cout_pad, int cin_pad,
                                     void *wt, void *stream);
 
-/* FP32 NCHW (n, c, h, w) -> BF16 NHWC with c_pad >= c channels (zero). */
+/* FP32 NCHW (n, c, h, w) -> BF16 NHWC with c_pad >= c channels (zero);
+ * c_pad a multiple of 8, y 16-byte aligned. */
 glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w,
                                  void *y, int c_pad, void *stream);
 
@@ -444,14 +445,16 @@ glbm_status glbm_nn_upsample2_nhwc(const void *x, int n, int c, int h, int w,
 
 /* Warm-start input of one medium of npix nodes (FP64 eps and K on the
  * device) -> x, 3 x npix FP32 (one NCHW sample): (eps - 0.05)/0.05,
- * (log10 K + 2)/2 and log10|G| + 6. */
+ * (log10 K + 2)/2 and log10|G| + 6, in FP32 arithmetic on the rounded
+ * inputs. */
 glbm_status glbm_nn_warm_features(const double *eps, const double *K,
                                   long long npix, double G, float *x,
                                   void *stream);
 
 /* Network output y (3 x npix FP32) -> FP64 warm-start fields on the device:
- * rho = 1 + y0 G rho_scale, ux = y1 K G / nu, uy = y2 K G / nu, ready for
- * glbm_init_equilibrium with device_ptrs = 1. */
+ * rho = 1 + y0 (G rho_scale), ux = (y1 K) (G / nu), uy = (y2 K) (G / nu)
+ * (the scalar factors formed first), ready for glbm_init_equilibrium with
+ * device_ptrs = 1. */
 glbm_status glbm_nn_warm_decode(const float *y, const double *K,
                                 long long npix, double G, double nu,
                                 double rho_scale, double *rho, double *ux,

@@ -285,16 +285,26 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 }
 
 // ---- NHWC layout kernels (memory-bound, grid-stride) --------------------------
-__global__ void k_nchw_to_nhwc(const float *__restrict__ x, int n, int c, int h, int w,
-                               __nv_bfloat16 *__restrict__ y, int cp) {
-    const long long total = (long long)n * h * w * cp;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int ch = int(i % cp);
-        const long long pix = i / cp;
-        const long long hw = (long long)h * w;
+// One thread per pixel: coalesced reads of each input plane, cp/8 16-byte
+// stores of the pixel's padded channel vector.
+__global__ void k_nchw_to_nhwc(const float *__restrict__ x, int n, int c, int h, int w, uint4 *__restrict__ y,
+                               int cp) {
+    const long long hw = (long long)h * w, total = (long long)n * hw;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < total;
+         pix += (long long)gridDim.x * blockDim.x) {
         const long long img = pix / hw, p = pix - img * hw;
-        y[i] = __float2bfloat16_rn(ch < c ? x[(img * c + ch) * hw + p] : 0.0f);
+        for (int c0 = 0; c0 < cp; c0 += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int a = c0 + 2 * j, b = a + 1;
+                const float va = a < c ? x[(img * c + a) * hw + p] : 0.0f;
+                const float vb = b < c ? x[(img * c + b) * hw + p] : 0.0f;
+                __nv_bfloat162 t = __floats2bfloat162_rn(va, vb);
+                pk[j] = *reinterpret_cast<uint32_t *>(&t);
+            }
+            y[pix * (cp / 8) + c0 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
     }
 }
 
@@ -352,28 +362,31 @@ __global__ void k_pack_w_tc(const float *__restrict__ w, int cout, int cin, int 
 
 // Network input of one medium (features of the warm start): channel 0
 // (eps - 0.05) / 0.05, channel 1 (log10 K + 2) / 2, channel 2 the constant
-// log10|G| + 6 (passed in), FP64 arithmetic rounded once to FP32.
+// log10|G| + 6 (passed in).  FP32 arithmetic on the rounded inputs (the
+// features are FP32 and feed a BF16 network; FP64 is slow on this GPU).
 __global__ void k_warm_features(const double *__restrict__ eps, const double *__restrict__ K, long long np,
                                 float g6, float *__restrict__ x) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
          i += (long long)gridDim.x * blockDim.x) {
-        x[i] = float(__ddiv_rn(__dsub_rn(eps[i], 0.05), 0.05));
-        x[np + i] = float(__ddiv_rn(__dadd_rn(log10(K[i]), 2.0), 2.0));
+        x[i] = (float(eps[i]) - 0.05f) * 20.0f;
+        x[np + i] = (log10f(float(K[i])) + 2.0f) * 0.5f;
         x[2 * np + i] = g6;
     }
 }
 
-// Network output -> warm-start fields: rho = 1 + y0 G s, u = y K G / nu
+// Network output -> warm-start fields: rho = 1 + y0 (G s), u = (y K) (G/nu)
 // (the network predicts the density deviation over G s and the velocity over
-// the local Darcy scale K G / nu), FP64, rounded in the written order.
-__global__ void k_warm_decode(const float *__restrict__ y, const double *__restrict__ K, long long np, double G,
-                              double nu, double s, double *__restrict__ rho, double *__restrict__ ux,
+// the local Darcy scale K G / nu), FP64, rounded in the written order with
+// the two scalar factors formed once on the host.
+__global__ void k_warm_decode(const float *__restrict__ y, const double *__restrict__ K, long long np, double gs,
+                              double g_nu, double *__restrict__ rho, double *__restrict__ ux,
                               double *__restrict__ uy) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np;
          i += (long long)gridDim.x * blockDim.x) {
-        rho[i] = __dadd_rn(1.0, __dmul_rn(__dmul_rn(double(y[i]), G), s));
-        ux[i] = __ddiv_rn(__dmul_rn(__dmul_rn(double(y[np + i]), K[i]), G), nu);
-        uy[i] = __ddiv_rn(__dmul_rn(__dmul_rn(double(y[2 * np + i]), K[i]), G), nu);
+        const double k = K[i];
+        rho[i] = __dadd_rn(1.0, __dmul_rn(double(y[i]), gs));
+        ux[i] = __dmul_rn(__dmul_rn(double(y[np + i]), k), g_nu);
+        uy[i] = __dmul_rn(__dmul_rn(double(y[2 * np + i]), k), g_nu);
     }
 }
 
@@ -499,11 +512,11 @@ extern "C" glbm_status glbm_nn_tc_pack_weights(const float *wf, int cout, int ci
 
 extern "C" glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w, void *y, int c_pad,
                                             void *stream) {
-    if (!x || !y || n < 1 || c < 1 || h < 1 || w < 1 || c_pad < c)
-        return tcfail(GLBM_EINVAL, "nn_nchw_to_nhwc: invalid sizes or pointers");
-    const long long total = (long long)n * h * w * c_pad;
-    k_nchw_to_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        x, n, c, h, w, static_cast<__nv_bfloat16 *>(y), c_pad);
+    if (!x || !y || n < 1 || c < 1 || h < 1 || w < 1 || c_pad < c || c_pad % 8 || (uintptr_t(y) & 15u))
+        return tcfail(GLBM_EINVAL, "nn_nchw_to_nhwc: need c_pad >= c, a multiple of 8, and 16-byte aligned y");
+    const long long total = (long long)n * h * w;
+    k_nchw_to_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, c, h, w,
+                                                                                   static_cast<uint4 *>(y), c_pad);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_nchw_to_nhwc launch");
 }
@@ -543,8 +556,8 @@ extern "C" glbm_status glbm_nn_warm_decode(const float *y, const double *K, long
                                            double rho_scale, double *rho, double *ux, double *uy, void *stream) {
     if (!y || !K || !rho || !ux || !uy || npix < 1 || !(nu > 0.0))
         return tcfail(GLBM_EINVAL, "nn_warm_decode: need y, K, rho, ux, uy, npix >= 1 and nu > 0");
-    k_warm_decode<<<grid_for(npix), 256, 0, static_cast<cudaStream_t>(stream)>>>(y, K, npix, G, nu, rho_scale,
-                                                                                  rho, ux, uy);
+    k_warm_decode<<<grid_for(npix), 256, 0, static_cast<cudaStream_t>(stream)>>>(y, K, npix, G * rho_scale,
+                                                                                  G / nu, rho, ux, uy);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_warm_decode launch");
 }

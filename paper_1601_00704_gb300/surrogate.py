@@ -430,4 +430,5 @@ def predict_device(net, eps, K, G, nu, tc=True):
 def decode(y, K, G, nu):
     """Network output (3, ny, nx) -> (rho, ux, uy) FP64."""
     y = np.asarray(y, dtype=np.float64)
-    return 1.0 + y[0] * G * RHO_SCALE, y[1] * K * G / nu, y[2] * K * G / nu
+    gs, g_nu = G * RHO_SCALE, G / nu
+    return 1.0 + y[0] * gs, y[1] * K * g_nu, y[2] * K * g_nu

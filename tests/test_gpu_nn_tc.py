@@ -184,7 +184,8 @@ def test_trained_network_tc_prediction(pkg):
 def test_device_features_and_decode_match_host(pkg):
     """The device-resident warm-start plumbing computes what the host
     definitions (surrogate.features / decode) compute: decode bit for bit,
-    features to one FP32 rounding (log10 may differ in the last FP64 bit)."""
+    features within a few FP32 roundings (the kernel works in FP32 on the
+    rounded eps and K, the host in FP64)."""
     import torch
 
     import media
@@ -199,7 +200,8 @@ def test_device_features_and_decode_match_host(pkg):
     assert lib.glbm_nn_warm_features(_vp(eps_d), _vp(K_d), 64 * 64, T.G, _vp(x), _stream()) == 0
     ref = surrogate.features(m["eps"], K, T.G)
     got = x.cpu().numpy()
-    np.testing.assert_allclose(got[:2], ref[:2], rtol=2.0 ** -23, atol=0)
+    # |feature| <= ~3: a few ulps of FP32 at that magnitude
+    np.testing.assert_allclose(got[:2], ref[:2], rtol=0, atol=2e-6)
     np.testing.assert_allclose(got[2], ref[2], rtol=0, atol=1e-9)  # log10|G| + 6, host libm on both sides
 
     y = np.random.default_rng(3).normal(size=(3, 64, 64)).astype(np.float32)
