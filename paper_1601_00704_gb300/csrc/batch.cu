@@ -61,6 +61,7 @@ k_batch_step(const T *__restrict__ src_all, T *__restrict__ dst_all,
              const BTile *__restrict__ tiles, const BMed *__restrict__ meds, Phys<typename Store<T>::R> ph,
              StepClock *__restrict__ clock, double *__restrict__ partial, float *__restrict__ pmax) {
     constexpr int VEC = kVecOf<T>;
+    pdl_enter();
     const BTile t = tiles[blockIdx.x];
     const BMed m = meds[t.med];
     Geo geo;
@@ -296,11 +297,13 @@ void launch_bstep_t(glbm_batch *h, bool reduce) {
     const T *src = static_cast<const T *>(h->buf[h->parity]);
     T *dst = static_cast<T *>(h->buf[h->parity ^ 1]);
     if (reduce)
-        k_batch_step<T, THREADS, WALLS, true><<<h->ntiles, THREADS, 0, h->stream>>>(
-            src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock, h->partial, nullptr);
+        launch_kernel(k_batch_step<T, THREADS, WALLS, true>, dim3(h->ntiles), dim3(THREADS), h->stream,
+                      h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
+                      h->partial, nullptr);
     else
-        k_batch_step<T, THREADS, WALLS, false><<<h->ntiles, THREADS, 0, h->stream>>>(
-            src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock, h->partial, nullptr);
+        launch_kernel(k_batch_step<T, THREADS, WALLS, false>, dim3(h->ntiles), dim3(THREADS), h->stream,
+                      h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
+                      h->partial, nullptr);
     h->launches++;
     h->parity ^= 1;
 }

@@ -132,12 +132,15 @@ glbm_status launch_step_t(glbm *h, bool reduce) {
     const R *e = static_cast<const R *>(h->coef[1]);
     const R *b = static_cast<const R *>(h->coef[2]);
     const dim3 grid = step_grid(geo);
+    const bool pdl = h->stream != nullptr;
+    cudaError_t err;
     if (reduce)
-        k_step<T, VEC, WALLS, FORCH, true>
-            <<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial, h->pmax);
+        err = launch_kernel(k_step<T, VEC, WALLS, FORCH, true>, grid, dim3(kThreads), h->stream, pdl, src, dst, a, e,
+                            b, geo, ph, h->partial, h->pmax);
     else
-        k_step<T, VEC, WALLS, FORCH, false>
-            <<<grid, kThreads, 0, h->stream>>>(src, dst, a, e, b, geo, ph, h->partial, h->pmax);
+        err = launch_kernel(k_step<T, VEC, WALLS, FORCH, false>, grid, dim3(kThreads), h->stream, pdl, src, dst, a,
+                            e, b, geo, ph, h->partial, h->pmax);
+    if (err != cudaSuccess) return fail(h, GLBM_ECUDA, "step launch: %s", cudaGetErrorString(err));
     h->launches++;
     h->tstep++;
     h->cur ^= 1;

@@ -45,6 +45,7 @@
 #include <cstdint>
 #include <cstring>
 #include <type_traits>
+#include <utility>
 
 namespace {
 
@@ -633,6 +634,36 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
 // writes this block's FP64 sums of u_x, u_y to partial[2*block] and, for
 // 16-bit storage, the largest stored magnitude |g*S| to pmax[block].
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  A step kernel launched with programmatic
+// stream serialisation may be scheduled while the previous kernel of the
+// stream drains.  It waits here, before touching any global memory (reads of
+// the previous step's output and writes into the buffer that step read), for
+// that kernel to complete and flush; then it lets the next launch start
+// placing its blocks, so launch latency and the last partial wave overlap.
+// Without the launch attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host: launch `kern` on `st`, with programmatic stream serialisation when
+// `pdl` (callers pass it for non-default streams).
+template <typename... P, typename... A>
+inline cudaError_t launch_kernel(void (*kern)(P...), dim3 grid, dim3 block, cudaStream_t st, bool pdl,
+                                 A &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 // Grid: x = blocks of a row (geo.bpr), row y = blockIdx.y + kMaxGridY *
 // blockIdx.z (step_grid).  Blocks of 128 threads resident per SM, fixed by
 // measurement on GB300: FP32 and FP16 fit 64 registers (8 blocks, 32 warps);
@@ -650,6 +681,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T>)
 k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::R *__restrict__ alpha,
        const typename Store<T>::R *__restrict__ epsv, const typename Store<T>::R *__restrict__ betav,
        Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ partial, float *__restrict__ pmax) {
+    pdl_enter();
     const int y = int(blockIdx.y) + kMaxGridY * int(blockIdx.z);
     if (y >= geo.ny) return;  // padding of the last z slice (whole block)
     const int bx = int(blockIdx.x);
