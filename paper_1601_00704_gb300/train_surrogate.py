@@ -260,7 +260,7 @@ def infer_timing(net, n, seed=4242, reps=3, tc=True):
             "ms_per_prediction": e0.elapsed_time(e1) / reps}
 
 
-def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
+def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, check=100, log=print):
     """Cold vs surrogate-started runs on an unseen n x n medium of the
     training recipe: steps and time to |K_app/K_ref - 1| <= 1e-3 (K_ref: FP32
     run to relative change < ref_tol per 10^4 steps), plus the raw
@@ -297,17 +297,17 @@ def warm_start_study(net, n=2048, seed=4242, ref_tol=1e-6, log=print):
     if net.tc_error():
         raise RuntimeError("tensor-core pipeline reported a timeout")
     k_raw = NU * float(fields[1].cpu().numpy().mean()) / G
-    runs = {"cold_f32": time_to_k(pkg, eps_d, K_d, k_ref),
-            "warm_f32": time_to_k(pkg, eps_d, K_d, k_ref, init=fields),
-            "cold_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16"),
-            "warm_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", init=fields)}
+    runs = {"cold_f32": time_to_k(pkg, eps_d, K_d, k_ref, check=check),
+            "warm_f32": time_to_k(pkg, eps_d, K_d, k_ref, init=fields, check=check),
+            "cold_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", check=check),
+            "warm_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", init=fields, check=check)}
     for r in ("warm_f32", "warm_bf16"):
         runs[r]["seconds_with_inference"] = runs[r]["seconds"] + infer_s
     base = runs["cold_f32"]["seconds"]
     out = {"workload": f"{n}x{n} medium of the training recipe, unseen seed {seed} (P {m['P'] / 1e6:.1f} MPa)",
            "k_ref": k_ref, "k_ref_from": f"FP32 cold run to relative change < {ref_tol:g} per 1e4 steps "
                                          f"({ref_steps} steps, converged={conv}, {ref_s:.1f} s)",
-           "criterion": "|K_app/K_ref - 1| <= 1e-3, checked every 1000 steps",
+           "criterion": f"|K_app/K_ref - 1| <= 1e-3, checked every {check} steps",
            "surrogate_raw_k_app_rel_err": k_raw / k_ref - 1, "inference_s": infer_s,
            "inference": "device-resident: features kernel, tensor-core (tcgen05) U-Net, decode kernel",
            "inference_fp32_kernels_s": infer32_s, "runs": runs,
