@@ -500,8 +500,9 @@ def sweep(a):
 
 
 def warm_start(a):
-    """Cold vs surrogate-initialised runs (FP32 and BF16) on an unseen 2048^2
-    medium of the surrogate's training recipe, with the committed weights."""
+    """Cold vs surrogate-initialised runs (FP32 and BF16) on three unseen
+    2048^2 media of the surrogate's training recipe, with the committed
+    weights."""
     from paper_1601_00704_gb300 import surrogate
     from paper_1601_00704_gb300 import train_surrogate as T
     path = T.DEFAULT_WEIGHTS
