@@ -45,6 +45,8 @@ CASES = [
     (1, 8, 8, 128, 128, 128, 3, True, False),   # smaller than one tile (rows beyond the image)
     (2, 32, 40, 32, 0, 16, 1, False, True),     # 1x1 head, FP32 NCHW output of 3 channels
     (1, 64, 256, 64, 0, 64, 3, True, False),    # several full 128-pixel tiles per row
+    (2, 5, 130, 64, 32, 48, 3, False, False),   # one-row tiles, two input tensors, a 2-pixel last tile
+    (1, 3, 384, 128, 128, 128, 3, True, False), # one-row tiles at the widest channel counts
 ]
 
 
@@ -137,7 +139,7 @@ def test_nhwc_layout_kernels(pkg):
     assert torch.equal(up.cpu(), ref_up)
 
 
-@pytest.mark.parametrize("levels,max_ch,size", [(3, 64, 32), (4, None, 64)])
+@pytest.mark.parametrize("levels,max_ch,size", [(3, 64, 32), (4, None, 64), (3, 64, 256)])
 def test_unet_forward_tc_matches_fp32(pkg, levels, max_ch, size):
     """Random-initialised network: the tensor-core forward pass agrees with the
     FP32 kernels to the BF16 activation rounding accumulated over the layers."""
