@@ -45,6 +45,7 @@ TAU = 1.0
 # bytes moved per node update by the fused step kernel (algorithmic):
 # 9 populations read + 9 written, plus the packed coefficients (alpha, eps).
 ELEM = {"f32": 4, "f64": 8, "f16": 2, "bf16": 2}
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (context beside the measured copy bandwidth)
 COEF = {"f32": 8, "f64": 16, "f16": 8, "bf16": 8}
 
 
@@ -603,7 +604,9 @@ def run_ours(a, world, rank, local):
             "frac": achieved / peak, "traffic": ncu_traffic(a.storage, a.nx, a.ny),
             "peak_kind": peak_kind, "bytes_per_node_update": bpu,
             "kernel": f"k_step<{a.storage}> (fused pull-stream + collide)",
-            "launch_us": per_launch_s * 1e6}
+            "launch_us": per_launch_s * 1e6,
+            "nominal": {"peak": NOMINAL_HBM_GBS, "frac": achieved / NOMINAL_HBM_GBS,
+                        "what": "GB300 HBM3e nominal bandwidth"}}
 
     e2e = None
     if not a.no_e2e:
