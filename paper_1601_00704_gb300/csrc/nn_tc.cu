@@ -15,7 +15,8 @@
 //    the 64-byte swizzle that the MMA's shared-memory descriptors read;
 //  * the input channels may come from two tensors (c0 channels of x0, then
 //    c1 of x1): the decoder's skip concatenation is never materialised;
-//  * one CTA per output tile with a 3-stage TMA ring (short, so that 4-6
+//  * one CTA per output tile (two tiles stacked in y, sharing every weight
+//    slice, when cout <= 64) with a 3-stage TMA ring (short, so that 4-6
 //    CTAs share an SM and hide each other's latency): warp 0 issues TMA,
 //    warp 1 issues tcgen05.mma
 //    into a TMEM accumulator, warps 2-5 read it back (tcgen05.ld), add the
@@ -160,7 +161,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
 
 struct TcConvArgs {
     int n, h, w, taps, nchunk0, nchunk, cout, tw, th;
-    uint32_t tmem_cols;
+    uint32_t tmem_cols;  // MT accumulators of acc_cols columns
+    uint32_t acc_cols;
     const float *bias;
     void *y;
     long long ys;  // output pixel stride (elements), NHWC output
@@ -168,6 +170,9 @@ struct TcConvArgs {
     int *err;
 };
 
+// MT output tiles per CTA, stacked in y (tile t covers rows y0 + t th ..):
+// they share every weight slice and accumulate into MT TMEM accumulators.
+template <int MT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
           const __grid_constant__ CUtensorMap mapB, const TcConvArgs a) {
@@ -176,13 +181,13 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     const int stage_b = a.cout * TC_KC * 2;
     uint8_t *sA = smem;
     constexpr int S = TC_STAGES;
-    uint8_t *sB = smem + S * TC_STAGE_A;
+    uint8_t *sB = smem + S * MT * TC_STAGE_A;
     __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x0 = blockIdx.x * a.tw, y0 = blockIdx.y * a.th, img = blockIdx.z;
+    const int x0 = blockIdx.x * a.tw, y0 = blockIdx.y * (MT * a.th), img = blockIdx.z;
     const int iters = a.taps * a.nchunk;
 
     if (threadIdx.x == 0) {
@@ -202,18 +207,22 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint32_t bytes = uint32_t(a.tw * a.th * TC_KC * 2 + stage_b);
+            const uint32_t bytes = uint32_t(MT * a.tw * a.th * TC_KC * 2 + stage_b);
             for (int i = 0; i < iters; ++i) {
                 const int s = i % S, use = i / S;
                 if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 1)) break;
                 const int tap = i / a.nchunk, ch = i - tap * a.nchunk;
                 const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
                 mbar_expect_tx(&full[s], bytes);
-                if (ch < a.nchunk0)
-                    tma_load_4d(sA + s * TC_STAGE_A, &mapA0, &full[s], ch * TC_KC, x0 + dx, y0 + dy, img);
-                else
-                    tma_load_4d(sA + s * TC_STAGE_A, &mapA1, &full[s], (ch - a.nchunk0) * TC_KC, x0 + dx, y0 + dy,
-                                img);
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    uint8_t *dst = sA + (s * MT + t) * TC_STAGE_A;
+                    const int yt = y0 + t * a.th + dy;
+                    if (ch < a.nchunk0)
+                        tma_load_4d(dst, &mapA0, &full[s], ch * TC_KC, x0 + dx, yt, img);
+                    else
+                        tma_load_4d(dst, &mapA1, &full[s], (ch - a.nchunk0) * TC_KC, x0 + dx, yt, img);
+                }
                 tma_load_3d(sB + s * stage_b, &mapB, &full[s], ch * TC_KC, 0, tap);
             }
         }
@@ -228,11 +237,15 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
                     break;
                 }
                 tc_fence_after();
-                const uint64_t ad = sdesc_k64(sA + s * TC_STAGE_A), bd = sdesc_k64(sB + s * stage_b);
+                const uint64_t bd = sdesc_k64(sB + s * stage_b);
 #pragma unroll
-                for (int kk = 0; kk < TC_KC / 16; ++kk)  // K = 16 per MMA: 32 bytes along the row
-                    umma_bf16(tmem, ad + uint64_t((kk * 32) >> 4), bd + uint64_t((kk * 32) >> 4), idesc,
-                              (i > 0 || kk > 0) ? 1u : 0u);
+                for (int t = 0; t < MT; ++t) {
+                    const uint64_t ad = sdesc_k64(sA + (s * MT + t) * TC_STAGE_A);
+#pragma unroll
+                    for (int kk = 0; kk < TC_KC / 16; ++kk)  // K = 16 per MMA: 32 bytes along the row
+                        umma_bf16(tmem + uint32_t(t) * a.acc_cols, ad + uint64_t((kk * 32) >> 4),
+                                  bd + uint64_t((kk * 32) >> 4), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
                 umma_commit(&empty[s]);
             }
             if (ok) umma_commit(&done);
@@ -241,14 +254,14 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
         const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 3);
         tc_fence_after();
-        if (have) {
+        for (int t = 0; t < MT && have; ++t) {
             const int m = q * 32 + lane;
-            const int px = x0 + m % a.tw, py = y0 + m / a.tw;
+            const int px = x0 + m % a.tw, py = y0 + t * a.th + m / a.tw;
             const bool ok = m < a.tw * a.th && px < a.w && py < a.h;
             const long long pix = ((long long)img * a.h + py) * a.w + px;
             for (int c = 0; c < a.cout; c += 16) {
                 float v[16];
-                tmem_ld16(tmem + (uint32_t(q * 32) << 16) + uint32_t(c), v);
+                tmem_ld16(tmem + uint32_t(t) * a.acc_cols + (uint32_t(q * 32) << 16) + uint32_t(c), v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     v[j] += a.bias[c + j];
@@ -454,7 +467,10 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv: cuTensorMapEncodeTiled is not available");
     const int tw = w < TC_M ? w : TC_M;
     const int th = TC_M / tw;
-    const long long gy = (h + th - 1) / th;
+    // two tiles per CTA for narrow outputs (cout <= 64): shared weight slices,
+    // more tiles in flight per SM where the layer is latency-bound
+    const int mt = cout <= 64 ? 2 : 1;
+    const long long gy = (h + th * mt - 1) / (th * mt);
     if (gy > 65535 || n > 65535) return tcfail(GLBM_EINVAL, "nn_tc_conv: image too tall or batch too large");
 
     CUtensorMap mA0, mA1, mB;
@@ -481,8 +497,9 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     a.cout = cout;
     a.tw = tw;
     a.th = th;
-    a.tmem_cols = 32;
-    while (a.tmem_cols < uint32_t(cout)) a.tmem_cols <<= 1;
+    a.acc_cols = 32;
+    while (a.acc_cols < uint32_t(cout)) a.acc_cols <<= 1;
+    a.tmem_cols = a.acc_cols * uint32_t(mt);
     a.bias = bias;
     a.y = y;
     a.ys = ys;
@@ -490,11 +507,12 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     a.f32_nchw = f32_nchw ? 1 : 0;
     a.cout_store = f32_nchw ? cout_store : cout;
     a.err = err;
-    const size_t smem = 1024 + size_t(TC_STAGES) * (TC_STAGE_A + size_t(cout) * TC_KC * 2);
-    cudaError_t e = cudaFuncSetAttribute(k_tc_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const size_t smem = 1024 + size_t(TC_STAGES) * (size_t(mt) * TC_STAGE_A + size_t(cout) * TC_KC * 2);
+    const auto kern = mt == 2 ? k_tc_conv<2> : k_tc_conv<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute");
     const dim3 grid(unsigned((w + tw - 1) / tw), unsigned(gy), unsigned(n));
-    k_tc_conv<<<grid, TC_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(mA0, mA1, mB, a);
+    kern<<<grid, TC_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(mA0, mA1, mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch");
 }
