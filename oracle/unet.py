@@ -20,7 +20,10 @@ a 1x1 head without activation.
 
 Pins (tests/test_oracle_unet.py): finite differences of the loss for every
 parameter tensor and for the input; single-channel convolution against
-scipy.signal.correlate2d; pooling/upsampling adjointness.
+scipy.signal.correlate2d; pooling/upsampling adjointness; hand-computed
+values of the pool, its gradient and the weighted loss on 4x4 arrays (these
+fail for a sum pool, a gradient without its 1/4, a loss averaged over the
+channels too or one without its channel weights).
 """
 
 from __future__ import annotations
