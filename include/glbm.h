@@ -166,7 +166,8 @@ glbm_status glbm_counters(glbm_t h, long long *steps, long long *launches);
  *           post-collision state, laid out [9][plane] (plane i holds node
  *           y*nx + x), D2Q9 order as in glbm_get_distributions.  Read only.
  *   g_dst   device, same layout, receives the state after the step; must not
- *           overlap g_src.  Start from zeros for f_eq(rho = 1, u = 0).
+ *           overlap g_src or the coefficient arrays.  Start from zeros for
+ *           f_eq(rho = 1, u = 0).
  *   alpha   device [ny][nx] FP32: eps*nu/K per node, nu = (tau - 1/2)/3
  *           (0 for K = +inf).
  *   eps     device [ny][nx] FP32 porosity.
@@ -181,14 +182,20 @@ glbm_status glbm_counters(glbm_t h, long long *steps, long long *launches);
  *
  * Limit: the lattice may need at most 65536 reduction blocks, where one
  * block covers 512 nodes of a row when nx is a multiple of 4 (else 128):
- * e.g. 4096 x 8192 fits.  Larger lattices, misaligned arrays and other bad
- * arguments return GLBM_EINVAL with a message in glbm_last_error(NULL).
+ * e.g. 4096 x 8192 fits.  Larger lattices, misaligned arrays, a g_dst or
+ * mean_u that overlaps any array the step reads (g_src, alpha, eps, beta;
+ * mean_u may not overlap g_dst either) and other bad arguments return
+ * GLBM_EINVAL with a message in glbm_last_error(NULL).
  *
  * The first call on each device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one scratch array, which
- * keeps the last call's contents (the status is cleared at the start of each
- * call): calls that overlap on the GPU, e.g. on two streams at once, race.
+ * before any stream capture.  The address is kept for the life of the
+ * process: a cudaDeviceReset (or anything else that destroys and recreates
+ * the device's primary context) may move the array and leave the kept
+ * address stale, so do not call this entry point on a device after resetting
+ * it.  Every call shares the one scratch array, which keeps the last call's
+ * contents (the status is cleared at the start of each call): calls that
+ * overlap on the GPU, e.g. on two streams at once, race.
  */
 glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst,
                                      const float *alpha, const float *eps,

@@ -726,6 +726,12 @@ glbm_status noalloc_scratch(double **out) {
     return GLBM_OK;
 }
 
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+    if (!a || !b || !na || !nb) return false;
+    const uintptr_t x = uintptr_t(a), y = uintptr_t(b);
+    return x < y + nb && y < x + na;
+}
+
 template <int VEC, bool WALLS, bool FORCH>
 void noalloc_launch(const float *src, float *dst, const float *a, const float *e, const float *b, const Geo &geo,
                     const Phys<float> &ph, double *partial, cudaStream_t st) {
@@ -740,7 +746,6 @@ extern "C" glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst
                                                 unsigned flags, double *mean_u, void *stream) {
     if (!g_src || !g_dst || !alpha || !eps || !mean_u)
         return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: g_src, g_dst, alpha, eps and mean_u are required");
-    if (g_src == g_dst) return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: g_src and g_dst must differ");
     if (nx < 2 || ny < 2 || (long long)nx * ny >= (1ll << 31))
         return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: need nx, ny >= 2 and nx*ny < 2^31");
     if (plane < (long long)nx * ny || plane % 4 != 0)
@@ -763,6 +768,24 @@ extern "C" glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst
                             "step_reduce_noalloc: lattice needs %lld reduction blocks but the fixed scratch "
                             "holds %d (one block covers %d nodes of a row)",
                             blocks, kNoAllocMaxBlocks, vec * kThreads);
+    // The pull-stream reads g_src while the step writes g_dst: any overlap
+    // between the buffer written and a buffer read gives wrong results.
+    const size_t fbytes = size_t(9) * size_t(plane) * sizeof(float);
+    const size_t cbytes = size_t(nx) * size_t(ny) * sizeof(float);
+    struct Range {
+        const void *p;
+        size_t n;
+        const char *name;
+    };
+    const Range reads[] = {{g_src, fbytes, "g_src"}, {alpha, cbytes, "alpha"}, {eps, cbytes, "eps"},
+                           {beta, beta ? cbytes : 0, "beta"}};
+    const Range writes[] = {{g_dst, fbytes, "g_dst"}, {mean_u, 2 * sizeof(double), "mean_u"}};
+    for (const Range &w : writes)
+        for (const Range &r : reads)
+            if (ranges_overlap(w.p, w.n, r.p, r.n))
+                return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: %s overlaps %s", w.name, r.name);
+    if (ranges_overlap(g_dst, fbytes, mean_u, 2 * sizeof(double)))
+        return noalloc_fail(GLBM_EINVAL, "step_reduce_noalloc: mean_u overlaps g_dst");
     double *scratch = nullptr;
     if (glbm_status s = noalloc_scratch(&scratch)) return s;
     double *partial = scratch;

@@ -91,3 +91,57 @@ def test_noalloc_rejects_oversize_lattice(env):
                                       nx, ny, nx * ny, 1.0, 1e-6, 0.0, 0, ptr(mean), None)
     assert rc == -1
     assert b"fixed scratch" in lib.glbm_last_error(None)
+
+
+def test_noalloc_rejects_overlapping_buffers(env):
+    """A destination that overlaps a buffer the step reads (here g_dst
+    starting inside g_src, or mean_u inside alpha) is refused with EINVAL
+    before anything is enqueued."""
+    pkg, lib, torch = env
+    nx, ny = 64, 8
+    plane = nx * ny
+    f = torch.zeros(2 * 9 * plane, dtype=torch.float32, device="cuda")
+    coef = torch.ones(2 * plane, dtype=torch.float32, device="cuda")
+    mean = torch.zeros(2, dtype=torch.float64, device="cuda")
+    rc = lib.glbm_step_reduce_noalloc(ptr(f), ptr(f[9 * plane - 64:]), ptr(coef), ptr(coef[plane:]), None,
+                                      nx, ny, plane, 1.0, 1e-6, 0.0, 0, ptr(mean), None)
+    assert rc == -1 and b"overlaps" in lib.glbm_last_error(None)
+    rc = lib.glbm_step_reduce_noalloc(ptr(f), ptr(f[9 * plane:]), ptr(coef), ptr(coef[plane:]), None,
+                                      nx, ny, plane, 1.0, 1e-6, 0.0, 0, ptr(coef[4:]), None)
+    assert rc == -1 and b"overlaps" in lib.glbm_last_error(None)
+    # disjoint buffers are accepted
+    rc = lib.glbm_step_reduce_noalloc(ptr(f), ptr(f[9 * plane:]), ptr(coef), ptr(coef[plane:]), None,
+                                      nx, ny, plane, 1.0, 1e-6, 0.0, 0, ptr(mean), None)
+    assert rc == 0, lib.glbm_last_error(None).decode()
+    torch.cuda.synchronize()
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """After the first call (which looks up the scratch array's address), a
+    run of further calls leaves the device's free memory and the caching
+    allocator's reservation unchanged."""
+    pkg, lib, torch = env
+    nx, ny = 512, 256
+    plane = nx * ny
+    f = torch.zeros(2 * 9 * plane, dtype=torch.float32, device="cuda")
+    coef = torch.full((2 * plane,), 0.5, dtype=torch.float32, device="cuda")
+    mean = torch.zeros(2, dtype=torch.float64, device="cuda")
+    halves = (f[:9 * plane], f[9 * plane:])
+
+    def call(k):
+        rc = lib.glbm_step_reduce_noalloc(ptr(halves[k % 2]), ptr(halves[(k + 1) % 2]), ptr(coef),
+                                          ptr(coef[plane:]), None, nx, ny, plane, 1.0, 1e-6, 0.0, 0,
+                                          ptr(mean), None)
+        assert rc == 0, lib.glbm_last_error(None).decode()
+
+    call(0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for k in range(1, 21):
+        call(k)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0
+    assert torch.cuda.memory_reserved() == reserved0
+    assert np.isfinite(mean.cpu().numpy()).all()
