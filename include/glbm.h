@@ -204,8 +204,38 @@ glbm_status glbm_step_reduce_noalloc(const float *g_src, float *g_dst,
                                      double gy, unsigned flags,
                                      double *mean_u, void *stream);
 
+/*
+ * Checkpoint and resume (no counterpart in the paper: long runs of the time
+ * loop are restartable).  glbm_save writes the handle's current
+ * distributions, packed medium coefficients, body force, step counts, FP16
+ * scale, stochastic-rounding seed and convergence history to the file
+ * `path` (overwritten), with a checksum; it waits for the stream.
+ * glbm_load reads such a file into a handle created with the same nx, ny,
+ * tau, storage and flags (no glbm_set_medium needed) and replaces its whole
+ * state; continuing from there gives the same bits as the run that was
+ * saved would have.  The file is host-endian and not meant to move between
+ * machines of different byte order.
+ * Errors: EINVAL (cannot open/read/write, not a checkpoint, another
+ * geometry or format, checksum mismatch; the handle is then unchanged),
+ * ESTATE (save before any medium), ECUDA.
+ */
+glbm_status glbm_save(glbm_t h, const char *path);
+glbm_status glbm_load(glbm_t h, const char *path);
+
 /* Release all device memory of the handle.  NULL-safe. */
 void glbm_destroy(glbm_t h);
+
+/*
+ * Test hook for the error paths (no counterpart in the paper): the kernel
+ * launch of glbm_step or glbm_batch_step that comes `after` launches from
+ * now (0 = the next one) is refused on the host with GLBM_ECUDA, as a
+ * rejected cudaLaunchKernelEx would be, without calling CUDA, so nothing
+ * faults.  A refusal while a chunk is being captured into a CUDA graph ends
+ * and discards the capture and leaves the handle's state, step count and
+ * launch count as they were before that chunk.  after < 0 switches the hook
+ * off (the default).  Process-wide; not for production use.
+ */
+void glbm_debug_fail_launch(long long after);
 
 /* ===========================================================================
  * Batched media: many lattices of uneven size advanced together.

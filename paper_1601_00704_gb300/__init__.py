@@ -34,7 +34,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_init_equilibrium", "glbm_step", "glbm_mean_velocity",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
-           "glbm_step_reduce_noalloc",
+           "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -84,6 +84,9 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_get_distributions": ([h, _VP, i], i),
         "glbm_counters": ([h, C.POINTER(ll), C.POINTER(ll)], i),
         "glbm_destroy": ([h], None),
+        "glbm_debug_fail_launch": ([ll], None),
+        "glbm_save": ([h, C.c_char_p], i),
+        "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),
         "glbm_step_reduce_noalloc": ([_VP, _VP, _VP, _VP, _VP, i, i, ll, d, d, d,
                                       C.c_uint, _VP, _VP], i),
@@ -278,6 +281,15 @@ class Solver:
         a = _Arg(out, shp, True)
         self._check(self._lib.glbm_get_distributions(self._h, a.ptr, int(a.device)))
         return out
+
+    def save(self, path):
+        """Checkpoint the whole solver state to a file (glbm_save)."""
+        self._check(self._lib.glbm_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        """Replace the solver state by a checkpoint of a solver of the same
+        geometry, tau, storage and boundaries (glbm_load)."""
+        self._check(self._lib.glbm_load(self._h, os.fsencode(path)))
 
     def counters(self):
         s, l = C.c_longlong(), C.c_longlong()

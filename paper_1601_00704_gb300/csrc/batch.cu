@@ -27,6 +27,7 @@
 #include <vector>
 
 extern __attribute__((visibility("hidden"))) thread_local char g_create_err[512];
+__attribute__((visibility("hidden"))) bool glbm_injected_failure();
 
 namespace {
 
@@ -283,7 +284,7 @@ glbm_status build_table(glbm_batch *h) {
 }
 
 template <typename T, int THREADS, bool WALLS>
-void launch_bstep_t(glbm_batch *h, bool reduce) {
+cudaError_t launch_bstep_t(glbm_batch *h, bool reduce) {
     using R = typename Store<T>::R;
     Phys<R> ph;
     ph.omega = R(1.0 / h->tau);
@@ -296,38 +297,47 @@ void launch_bstep_t(glbm_batch *h, bool reduce) {
     ph.sr = 1;
     const T *src = static_cast<const T *>(h->buf[h->parity]);
     T *dst = static_cast<T *>(h->buf[h->parity ^ 1]);
+    if (glbm_injected_failure()) return cudaErrorLaunchFailure;  // test hook: nothing is launched
+    cudaError_t e;
     if (reduce)
-        launch_kernel(k_batch_step<T, THREADS, WALLS, true>, dim3(h->ntiles), dim3(THREADS), h->stream,
-                      h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
-                      h->partial, nullptr);
+        e = launch_kernel(k_batch_step<T, THREADS, WALLS, true>, dim3(h->ntiles), dim3(THREADS), h->stream,
+                          h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
+                          h->partial, nullptr);
     else
-        launch_kernel(k_batch_step<T, THREADS, WALLS, false>, dim3(h->ntiles), dim3(THREADS), h->stream,
-                      h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
-                      h->partial, nullptr);
+        e = launch_kernel(k_batch_step<T, THREADS, WALLS, false>, dim3(h->ntiles), dim3(THREADS), h->stream,
+                          h->stream != nullptr, src, dst, h->coef[0], h->coef[1], h->dtiles, h->dmed, ph, h->dclock,
+                          h->partial, nullptr);
+    if (e != cudaSuccess) return e;
     h->launches++;
     h->parity ^= 1;
+    return cudaSuccess;
 }
 
 template <typename T>
-void launch_bstep_s(glbm_batch *h, bool reduce) {
+cudaError_t launch_bstep_s(glbm_batch *h, bool reduce) {
     const bool walls = !(h->flags & GLBM_PERIODIC_Y);
     switch (h->threads) {
-        case 64: walls ? launch_bstep_t<T, 64, true>(h, reduce) : launch_bstep_t<T, 64, false>(h, reduce); break;
-        case 256: walls ? launch_bstep_t<T, 256, true>(h, reduce) : launch_bstep_t<T, 256, false>(h, reduce); break;
-        default: walls ? launch_bstep_t<T, 128, true>(h, reduce) : launch_bstep_t<T, 128, false>(h, reduce); break;
+        case 64: return walls ? launch_bstep_t<T, 64, true>(h, reduce) : launch_bstep_t<T, 64, false>(h, reduce);
+        case 256: return walls ? launch_bstep_t<T, 256, true>(h, reduce) : launch_bstep_t<T, 256, false>(h, reduce);
+        default: return walls ? launch_bstep_t<T, 128, true>(h, reduce) : launch_bstep_t<T, 128, false>(h, reduce);
     }
 }
 
-void launch_bstep(glbm_batch *h, bool reduce) {
-    if (h->storage == GLBM_BF16DEV) launch_bstep_s<__nv_bfloat16>(h, reduce);
-    else launch_bstep_s<float>(h, reduce);
+cudaError_t launch_bstep(glbm_batch *h, bool reduce) {
+    if (h->storage == GLBM_BF16DEV) return launch_bstep_s<__nv_bfloat16>(h, reduce);
+    return launch_bstep_s<float>(h, reduce);
 }
 
-// Enqueue `chunk` steps (+ the per-medium reduction at the last one).
-void enqueue_chunk(glbm_batch *h, int chunk, double tol) {
-    for (int s = 0; s < chunk; ++s) launch_bstep(h, s == chunk - 1);
+// Enqueue `chunk` steps (+ the per-medium reduction at the last one); the
+// first failed launch stops it and is returned.
+cudaError_t enqueue_chunk(glbm_batch *h, int chunk, double tol) {
+    for (int s = 0; s < chunk; ++s)
+        if (cudaError_t e = launch_bstep(h, s == chunk - 1)) return e;
+    if (glbm_injected_failure()) return cudaErrorLaunchFailure;
     k_batch_finalize<<<h->nact, 256, 0, h->stream>>>(h->partial, h->dmed, h->dact, tol, h->dstat);
+    if (cudaError_t e = cudaGetLastError()) return e;
     h->launches++;
+    return cudaSuccess;
 }
 
 // Run one chunk, from a captured graph when the same (parity, length, test)
@@ -342,16 +352,32 @@ glbm_status run_chunk(glbm_batch *h, int chunk, double tol) {
             return GLBM_OK;
         }
     }
+    // a failure while capturing ends the capture, discards it and leaves the
+    // parity and launch count as they were (nothing has run)
     const int p0 = h->parity;
+    const long long l0 = h->launches;
     cudaGraph_t graph = nullptr;
     BCU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_chunk(h, chunk, tol);
+    const cudaError_t el = enqueue_chunk(h, chunk, tol);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-    if (e != cudaSuccess) return bfail(h, GLBM_ECUDA, "batch: graph capture failed: %s", cudaGetErrorString(e));
     cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return bfail(h, GLBM_ECUDA, "batch: graph instantiate failed: %s", cudaGetErrorString(e));
+    glbm_status st = GLBM_OK;
+    if (el != cudaSuccess)
+        st = bfail(h, GLBM_ECUDA, "batch: step launch failed: %s%s", cudaGetErrorString(el),
+                   el == cudaErrorLaunchFailure ? " (injected by the test hook)" : "");
+    else if (e != cudaSuccess)
+        st = bfail(h, GLBM_ECUDA, "batch: graph capture failed: %s", cudaGetErrorString(e));
+    if (!st) {
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) st = bfail(h, GLBM_ECUDA, "batch: graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st) {
+        (void)cudaGetLastError();
+        h->parity = p0;
+        h->launches = l0;
+        return st;
+    }
     h->graphs.push_back({p0, chunk, test, exec});
     BCU(h, cudaGraphLaunch(exec, h->stream));
     return GLBM_OK;

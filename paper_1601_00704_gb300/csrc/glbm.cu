@@ -12,9 +12,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "glbm_kernels.cuh"
 #include "setup_kernels.cuh"
@@ -25,6 +27,21 @@
 // Message buffer for failures without a handle (glbm_last_error(NULL)),
 // shared with the other translation units of the library.
 __attribute__((visibility("hidden"))) thread_local char g_create_err[512] = "";
+
+// Host-side fault injection for tests of the error paths
+// (glbm_debug_fail_launch): the launch that comes `g_fail_countdown`
+// launches from now is refused with GLBM_ECUDA, as a failed launch would be,
+// without calling CUDA.  Negative = off.  Shared with batch.cu.
+namespace {
+std::atomic<long long> g_fail_countdown{-1};
+}
+__attribute__((visibility("hidden"))) bool glbm_injected_failure() {
+    long long c = g_fail_countdown.load();
+    while (c >= 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+    }
+    return false;
+}
 
 struct glbm {
     int nx = 0, ny = 0;
@@ -54,13 +71,17 @@ struct glbm {
     uint32_t seed = 0x2545F491u;
     long long tstep = 0;      // time steps launched since the last reset
     long long steps = 0, launches = 0;
-    // chunks replayed from captured CUDA graphs (FP32/FP64 on a non-legacy
-    // stream): key = (buffer parity at start, steps, reduce at end, test)
+    // 16-bit storage: device copy of tstep, read by the step kernels of
+    // replayed graphs for their stochastic-rounding key
+    unsigned *dclock = nullptr;
+    // chunks replayed from captured CUDA graphs (any storage, on a
+    // non-legacy stream): key = (buffer parity at start, steps, reduce at
+    // end, test, tol, FP16 scale)
     struct Graph {
         int parity;
         long long chunk;
         int reduce, test;
-        double tol;
+        double tol, scale;
         cudaGraphExec_t exec;
     };
     Graph graphs[8];
@@ -111,21 +132,32 @@ Phys<R> make_phys(const glbm *h) {
     p.gy = R(h->gy);
     p.scale = R(h->scale);
     p.inv_scale = R(1.0 / h->scale);
-    p.step_key = mix32(uint32_t(h->tstep) * 0x9E3779B9u + h->seed);
+    p.step_key = step_key_of(uint32_t(h->tstep), h->seed);
     p.sr = h->sr ? 1 : 0;
+    p.seed = h->seed;
     return p;
 }
+
+bool injected_failure() { return glbm_injected_failure(); }
 
 int grid_1d(long long N) {
     long long b = (N + 255) / 256;
     return int(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
 }
 
+// One step kernel.  `clock_off` >= 0 (16-bit storage inside a graph
+// capture): the kernel takes its rounding key from the device step counter
+// plus clock_off, so that replays of the graph draw fresh bits.
 template <typename T, int VEC, bool WALLS, bool FORCH>
-glbm_status launch_step_t(glbm *h, bool reduce) {
+glbm_status launch_step_t(glbm *h, bool reduce, long long clock_off) {
     using R = typename Store<T>::R;
     const Geo geo = make_geo(h, VEC);
-    const Phys<R> ph = make_phys<R>(h);
+    Phys<R> ph = make_phys<R>(h);
+    if (Store<T>::kSmall && clock_off >= 0) {
+        ph.clock = h->dclock;
+        ph.step_off = uint32_t(clock_off);
+    }
+    if (injected_failure()) return fail(h, GLBM_ECUDA, "step launch: injected failure (test hook)");
     const T *src = static_cast<const T *>(h->buf[h->cur]);
     T *dst = static_cast<T *>(h->buf[h->cur ^ 1]);
     const R *a = static_cast<const R *>(h->coef[0]);
@@ -148,24 +180,24 @@ glbm_status launch_step_t(glbm *h, bool reduce) {
 }
 
 template <typename T>
-glbm_status launch_step(glbm *h, bool reduce) {
+glbm_status launch_step(glbm *h, bool reduce, long long co) {
     constexpr int V = kVecOf<T>;
     const bool walls = !(h->flags & GLBM_PERIODIC_Y);
     const bool vec = vec_width(h) > 1;
     if (vec) {
-        if (walls) return h->forch ? launch_step_t<T, V, true, true>(h, reduce) : launch_step_t<T, V, true, false>(h, reduce);
-        return h->forch ? launch_step_t<T, V, false, true>(h, reduce) : launch_step_t<T, V, false, false>(h, reduce);
+        if (walls) return h->forch ? launch_step_t<T, V, true, true>(h, reduce, co) : launch_step_t<T, V, true, false>(h, reduce, co);
+        return h->forch ? launch_step_t<T, V, false, true>(h, reduce, co) : launch_step_t<T, V, false, false>(h, reduce, co);
     }
-    if (walls) return h->forch ? launch_step_t<T, 1, true, true>(h, reduce) : launch_step_t<T, 1, true, false>(h, reduce);
-    return h->forch ? launch_step_t<T, 1, false, true>(h, reduce) : launch_step_t<T, 1, false, false>(h, reduce);
+    if (walls) return h->forch ? launch_step_t<T, 1, true, true>(h, reduce, co) : launch_step_t<T, 1, true, false>(h, reduce, co);
+    return h->forch ? launch_step_t<T, 1, false, true>(h, reduce, co) : launch_step_t<T, 1, false, false>(h, reduce, co);
 }
 
-glbm_status do_step(glbm *h, bool reduce) {
+glbm_status do_step(glbm *h, bool reduce, long long clock_off = -1) {
     switch (h->storage) {
-        case GLBM_F32: return launch_step<float>(h, reduce);
-        case GLBM_F64: return launch_step<double>(h, reduce);
-        case GLBM_F16DEV: return launch_step<__half>(h, reduce);
-        case GLBM_BF16DEV: return launch_step<__nv_bfloat16>(h, reduce);
+        case GLBM_F32: return launch_step<float>(h, reduce, clock_off);
+        case GLBM_F64: return launch_step<double>(h, reduce, clock_off);
+        case GLBM_F16DEV: return launch_step<__half>(h, reduce, clock_off);
+        case GLBM_BF16DEV: return launch_step<__nv_bfloat16>(h, reduce, clock_off);
     }
     return GLBM_EINVAL;
 }
@@ -176,10 +208,23 @@ int nparts(const glbm *h) {
 }
 
 glbm_status finalize(glbm *h, double tol) {
+    if (injected_failure()) return fail(h, GLBM_ECUDA, "finalize launch: injected failure (test hook)");
     k_finalize<<<1, 256, 0, h->stream>>>(h->partial, nparts(h), 1.0 / double(h->N), tol, h->dstat,
                                          h->elem == 2 ? h->pmax : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
     h->launches++;
     h->reduced = true;
+    return GLBM_OK;
+}
+
+// 16-bit storage: set (add = 0) or advance (add = 1) the device step counter.
+glbm_status clock_op(glbm *h, long long value, bool add) {
+    if (h->elem != 2) return GLBM_OK;
+    k_clock<<<1, 1, 0, h->stream>>>(h->dclock, unsigned(value), add ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "clock launch: %s", cudaGetErrorString(e));
+    h->launches++;
     return GLBM_OK;
 }
 
@@ -200,20 +245,22 @@ void drop_graphs(glbm *h) {
     h->ngraphs = 0;
 }
 
-bool graph_eligible(const glbm *h) {
-    return h->stream != nullptr && (h->storage == GLBM_F32 || h->storage == GLBM_F64);
-}
+bool graph_eligible(const glbm *h) { return h->stream != nullptr; }
 
 // Enqueue one chunk (chunk steps, the last one reducing when `reduce`, then
-// the finalize), directly or by replaying a captured graph of it.
+// the finalize), directly or by replaying a captured graph of it.  A failure
+// while capturing ends the capture, discards it and leaves the handle's
+// buffer parity, step and launch counts as they were; nothing has run.
 glbm_status run_chunk(glbm *h, long long chunk, bool reduce, double tol) {
     const int test = tol > 0.0;
+    const bool small = h->elem == 2;
     if (graph_eligible(h) && chunk >= 4) {
         for (int i = 0; i < h->ngraphs; ++i) {
             const glbm::Graph &g = h->graphs[i];
-            if (g.parity == h->cur && g.chunk == chunk && g.reduce == int(reduce) && g.test == test && g.tol == tol) {
+            if (g.parity == h->cur && g.chunk == chunk && g.reduce == int(reduce) && g.test == test &&
+                g.tol == tol && g.scale == h->scale) {
                 CU(h, cudaGraphLaunch(g.exec, h->stream));
-                h->launches += chunk + (reduce ? 1 : 0);
+                h->launches += chunk + (reduce ? 1 : 0) + (small ? 1 : 0);
                 h->tstep += chunk;
                 if (chunk % 2) h->cur ^= 1;
                 if (reduce) h->reduced = true;
@@ -222,23 +269,42 @@ glbm_status run_chunk(glbm *h, long long chunk, bool reduce, double tol) {
         }
         if (h->ngraphs == 8) drop_graphs(h);
         const int p0 = h->cur;
+        const long long t0 = h->tstep, l0 = h->launches;
+        const bool r0 = h->reduced;
         cudaGraph_t graph = nullptr;
         CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        for (long long s = 0; s < chunk; ++s) do_step(h, reduce && s == chunk - 1);
-        if (reduce) finalize(h, tol);
+        glbm_status st = GLBM_OK;
+        for (long long s = 0; s < chunk && !st; ++s) st = do_step(h, reduce && s == chunk - 1, small ? s : -1);
+        if (!st && reduce) st = finalize(h, tol);
+        if (!st) st = clock_op(h, chunk, true);
         cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-        if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "step: graph capture failed: %s", cudaGetErrorString(e));
         cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "step: graph instantiate failed: %s", cudaGetErrorString(e));
-        h->graphs[h->ngraphs++] = {p0, chunk, int(reduce), test, tol, exec};
+        if (!st && e != cudaSuccess)
+            st = fail(h, GLBM_ECUDA, "step: graph capture failed: %s", cudaGetErrorString(e));
+        if (!st) {
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess)
+                st = fail(h, GLBM_ECUDA, "step: graph instantiate failed: %s", cudaGetErrorString(e));
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (st) {
+            (void)cudaGetLastError();  // drop the capture's error state
+            h->cur = p0;
+            h->tstep = t0;
+            h->launches = l0;
+            h->reduced = r0;
+            return st;
+        }
+        h->graphs[h->ngraphs++] = {p0, chunk, int(reduce), test, tol, h->scale, exec};
         CU(h, cudaGraphLaunch(exec, h->stream));
         return GLBM_OK;
     }
     for (long long s = 0; s < chunk; ++s)
         if (glbm_status st = do_step(h, reduce && s == chunk - 1)) return st;
-    if (reduce) finalize(h, tol);
+    if (reduce)
+        if (glbm_status st = finalize(h, tol)) return st;
+    // keep the device step counter in step for later graph replays
+    if (graph_eligible(h)) return clock_op(h, h->tstep, false);
     return GLBM_OK;
 }
 
@@ -377,6 +443,7 @@ void release(glbm *h) {
     if (h->pmax) cudaFree(h->pmax), h->pmax = nullptr;
     if (h->dstat) cudaFree(h->dstat), h->dstat = nullptr;
     if (h->dflag) cudaFree(h->dflag), h->dflag = nullptr;
+    if (h->dclock) cudaFree(h->dclock), h->dclock = nullptr;
     if (h->stage) cudaFree(h->stage), h->stage = nullptr;
     if (h->hstat) cudaFreeHost(h->hstat), h->hstat = nullptr;
 }
@@ -426,8 +493,10 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
     if (e == cudaSuccess) e = cudaMalloc(&h->pmax, sizeof(float) * size_t(h->nparts_max));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstat, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dclock, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&h->hstat, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dclock, 0, sizeof(unsigned), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         glbm_status s = fail(nullptr, e == cudaErrorMemoryAllocation ? GLBM_ENOMEM : GLBM_ECUDA,
@@ -469,6 +538,7 @@ glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K, double
     CU(h, cudaMemsetAsync(h->buf[0], 0, size_t(9) * h->plane * h->elem, h->stream));
     CU(h, cudaMemsetAsync(h->buf[1], 0, size_t(9) * h->plane * h->elem, h->stream));
     if (glbm_status s = reset_status(h)) return s;
+    CU(h, cudaMemsetAsync(h->dclock, 0, sizeof(unsigned), h->stream));
     if (h->forch != (F_eps != 0.0)) drop_graphs(h);  // another kernel instantiation
     h->cur = 0;
     h->steps = 0;
@@ -532,6 +602,7 @@ glbm_status glbm_init_equilibrium(glbm_t h, const double *rho, const double *ux,
     init_eq_dispatch(h, d[0], d[1], d[2]);
     if (glbm_status s = launch_error(h)) return s;
     if (glbm_status s = reset_status(h)) return s;
+    CU(h, cudaMemsetAsync(h->dclock, 0, sizeof(unsigned), h->stream));
     h->steps = 0;
     h->tstep = 0;
     h->at_rest = !(rho || ux);
@@ -662,6 +733,148 @@ glbm_status glbm_counters(glbm_t h, long long *steps, long long *launches) {
     return GLBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  File layout (native byte order): a fixed header
+// (CkptHeader), then the current distributions as 9 planes of N stored
+// elements (no padding), then the coefficient planes alpha, eps and, with
+// Forchheimer, beta (N elements each).  An FNV-1a 64 checksum of everything
+// after the header guards against truncated or altered files.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];  // "GLBMCKP1"
+    unsigned version;
+    int nx, ny, storage;
+    unsigned flags;
+    int forch, at_rest, reduced, sr;
+    double tau, feps_mode, gx, gy, scale;
+    unsigned seed, pad;
+    long long tstep, steps;
+    DevStatus status;
+    unsigned long long checksum;
+};
+
+constexpr unsigned kCkptVersion = 1;
+
+void fnv1a(unsigned long long &h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+}
+
+struct File {
+    FILE *f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+glbm_status glbm_save(glbm_t h, const char *path) {
+    if (glbm_status s = check(h)) return s;
+    if (!path) return fail(h, GLBM_EINVAL, "save: path is NULL");
+    if (!h->has_medium) return fail(h, GLBM_ESTATE, "save: no medium set");
+    const size_t N = size_t(h->N);
+    const size_t fb = 9 * N * h->elem, cb = N * h->celem;
+    const int ncoef = h->forch ? 3 : 2;
+    std::vector<unsigned char> buf(fb + ncoef * cb);
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "GLBMCKP1", 8);
+    hd.version = kCkptVersion;
+    hd.nx = h->nx;
+    hd.ny = h->ny;
+    hd.storage = int(h->storage);
+    hd.flags = h->flags;
+    hd.forch = h->forch;
+    hd.at_rest = h->at_rest;
+    hd.reduced = h->reduced;
+    hd.sr = h->sr;
+    hd.tau = h->tau;
+    hd.feps_mode = h->feps_mode;
+    hd.gx = h->gx;
+    hd.gy = h->gy;
+    hd.scale = h->scale;
+    hd.seed = h->seed;
+    hd.tstep = h->tstep;
+    hd.steps = h->steps;
+    CU(h, cudaMemcpy2DAsync(buf.data(), N * h->elem, h->buf[h->cur], size_t(h->plane) * h->elem, N * h->elem, 9,
+                            cudaMemcpyDeviceToHost, h->stream));
+    for (int c = 0; c < ncoef; ++c)
+        CU(h, cudaMemcpyAsync(buf.data() + fb + c * cb, h->coef[c], cb, cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(&hd.status, h->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    hd.checksum = 14695981039346656037ull;
+    fnv1a(hd.checksum, buf.data(), buf.size());
+    File f;
+    f.f = fopen(path, "wb");
+    if (!f.f) return fail(h, GLBM_EINVAL, "save: cannot open %s for writing", path);
+    if (fwrite(&hd, sizeof(hd), 1, f.f) != 1 || fwrite(buf.data(), 1, buf.size(), f.f) != buf.size() ||
+        fflush(f.f) != 0)
+        return fail(h, GLBM_EINVAL, "save: writing %s failed", path);
+    return GLBM_OK;
+}
+
+glbm_status glbm_load(glbm_t h, const char *path) {
+    if (glbm_status s = check(h)) return s;
+    if (!path) return fail(h, GLBM_EINVAL, "load: path is NULL");
+    File f;
+    f.f = fopen(path, "rb");
+    if (!f.f) return fail(h, GLBM_EINVAL, "load: cannot open %s", path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, f.f) != 1 || memcmp(hd.magic, "GLBMCKP1", 8) != 0 ||
+        hd.version != kCkptVersion)
+        return fail(h, GLBM_EINVAL, "load: %s is not a checkpoint of this library version", path);
+    if (hd.nx != h->nx || hd.ny != h->ny || hd.storage != int(h->storage) || hd.flags != h->flags ||
+        hd.tau != h->tau)
+        return fail(h, GLBM_EINVAL,
+                    "load: checkpoint is %d x %d, storage %d, flags 0x%x, tau %g; handle is %d x %d, storage %d, "
+                    "flags 0x%x, tau %g",
+                    hd.nx, hd.ny, hd.storage, hd.flags, hd.tau, h->nx, h->ny, int(h->storage), h->flags, h->tau);
+    const size_t N = size_t(h->N);
+    const size_t fb = 9 * N * h->elem, cb = N * h->celem;
+    const int ncoef = hd.forch ? 3 : 2;
+    std::vector<unsigned char> buf(fb + ncoef * cb);
+    if (fread(buf.data(), 1, buf.size(), f.f) != buf.size())
+        return fail(h, GLBM_EINVAL, "load: %s is truncated", path);
+    unsigned long long sum = 14695981039346656037ull;
+    fnv1a(sum, buf.data(), buf.size());
+    if (sum != hd.checksum) return fail(h, GLBM_EINVAL, "load: checksum mismatch in %s", path);
+    // the other buffer's padding and contents are never read before written
+    CU(h, cudaMemcpy2DAsync(h->buf[0], size_t(h->plane) * h->elem, buf.data(), N * h->elem, N * h->elem, 9,
+                            cudaMemcpyHostToDevice, h->stream));
+    for (int c = 0; c < ncoef; ++c)
+        CU(h, cudaMemcpyAsync(h->coef[c], buf.data() + fb + c * cb, cb, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->dstat, &hd.status, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+    const unsigned clock = unsigned(hd.tstep);
+    CU(h, cudaMemcpyAsync(h->dclock, &clock, sizeof(unsigned), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));  // host staging goes out of scope
+    if (bool(hd.forch) != h->forch) drop_graphs(h);
+    if (hd.gx != h->gx || hd.gy != h->gy || hd.scale != h->scale) drop_graphs(h);
+    h->cur = 0;
+    h->forch = hd.forch;
+    h->feps_mode = hd.feps_mode;
+    h->at_rest = hd.at_rest;
+    h->reduced = hd.reduced;
+    h->sr = hd.sr;
+    h->gx = hd.gx;
+    h->gy = hd.gy;
+    h->scale = hd.scale;
+    h->seed = hd.seed;
+    h->tstep = hd.tstep;
+    h->steps = hd.steps;
+    h->has_medium = true;
+    return GLBM_OK;
+}
+
 void glbm_destroy(glbm_t h) {
     if (!h) return;
     cudaSetDevice(h->dev);
@@ -671,6 +884,8 @@ void glbm_destroy(glbm_t h) {
 }
 
 const char *glbm_last_error(glbm_t h) { return h ? h->err : g_create_err; }
+
+void glbm_debug_fail_launch(long long after) { g_fail_countdown.store(after < 0 ? -1 : after); }
 
 }  // extern "C"
 

@@ -188,7 +188,19 @@ struct Phys {
     R inv_scale; // 1/S
     uint32_t step_key;  // per-step key of the stochastic-rounding hash
     int sr;             // 16-bit storage: 1 = stochastic rounding, 0 = nearest
+    // 16-bit storage inside a replayed CUDA graph: when `clock` is set the
+    // kernel forms its key from the device step counter instead,
+    // step_key = mix32((*clock + step_off) * 0x9E3779B9 + seed), the same
+    // value the host forms for step *clock + step_off.
+    const unsigned *clock = nullptr;
+    uint32_t step_off = 0;
+    uint32_t seed = 0;
 };
+
+// Stochastic-rounding key of time step t (host and device agree).
+__host__ __device__ __forceinline__ uint32_t step_key_of(uint32_t t, uint32_t seed) {
+    return mix32(t * 0x9E3779B9u + seed);
+}
 
 struct Geo {
     int nx, ny;
@@ -682,6 +694,9 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
        const typename Store<T>::R *__restrict__ epsv, const typename Store<T>::R *__restrict__ betav,
        Geo geo, Phys<typename Store<T>::R> ph, double *__restrict__ partial, float *__restrict__ pmax) {
     pdl_enter();
+    if constexpr (Store<T>::kSmall) {
+        if (ph.clock) ph.step_key = step_key_of(*ph.clock + ph.step_off, ph.seed);
+    }
     const int y = int(blockIdx.y) + kMaxGridY * int(blockIdx.z);
     if (y >= geo.ny) return;  // padding of the last z slice (whole block)
     const int bx = int(blockIdx.x);
@@ -701,6 +716,14 @@ k_step(const T *__restrict__ src, T *__restrict__ dst, const typename Store<T>::
             if (threadIdx.x == 0) pmax[blk] = gm;
         }
     }
+}
+
+// Device step counter of 16-bit storage (see Phys::clock): set to a value
+// or advanced by a captured chunk's length, one thread, ordered on the
+// stream after the chunk's last step kernel.
+__global__ void k_clock(unsigned *__restrict__ clock, unsigned value, int add) {
+    pdl_enter();
+    *clock = add ? *clock + value : value;
 }
 
 // Device-side run status (A8 result and convergence test).

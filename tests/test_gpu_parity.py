@@ -254,11 +254,14 @@ def test_nan_detected(pkg):
     assert e.value.name == "GLBM_ENAN"
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
 def test_graph_replay_matches_direct_launches(pkg, storage):
     """On a user stream glbm_step replays captured chunk graphs; the result
     equals direct launches on the legacy stream bit for bit, including odd
-    chunk lengths, a partial last chunk and convergence tests."""
+    chunk lengths, a partial last chunk and convergence tests.  16-bit
+    storage takes its stochastic-rounding key from a device step counter
+    inside graphs and from the host otherwise: the keys, hence the bits,
+    agree (its launch count differs by the counter updates)."""
     import torch
     eps, K, _ = media.two_phase_medium(96, 40, seed=8)
     out = []
@@ -275,16 +278,20 @@ def test_graph_replay_matches_direct_launches(pkg, storage):
         out.append((s.distributions(), s.mean_velocity(), a, s.counters()))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
-    assert out[0][2] == out[1][2] and out[0][3] == out[1][3]
+    assert out[0][2] == out[1][2]
+    if storage in ("f32", "f64"):
+        assert out[0][3] == out[1][3]
+    else:
+        assert out[0][3][0] == out[1][3][0]
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_dependent_launch_matches_plain_launches(pkg, storage):
     """On a user stream the step kernels use programmatic dependent launch
     (the next step is placed while the previous drains and waits on the GPU
-    for it); on the legacy stream they launch plainly.  16-bit storage
-    replays no graphs, so this compares dependent launches step by step with
-    plain ones, bit for bit, on a lattice of several waves of blocks."""
+    for it); on the legacy stream they launch plainly.  This compares the
+    two bit for bit on a lattice of several waves of blocks (on the user
+    stream the 100-step chunks are replayed graphs)."""
     import torch
     eps, K, _ = media.two_phase_medium(512, 384, seed=12)
     out = []
