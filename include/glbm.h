@@ -127,6 +127,18 @@ glbm_status glbm_init_equilibrium(glbm_t h, const double *rho,
 glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every,
                       long long *steps_done, int *converged);
 
+/*
+ * Convergence test of glbm_step: converged once `patience` CONSECUTIVE
+ * checks each pass |Ux - Ux_prev| <= tol * |Ux| (default 1: the first pass).
+ * With 16-bit storage the stochastic rounding leaves a noise floor on Ux:
+ * near that floor two checks can agree by chance while the slow mode is
+ * still drifting, and a patience of a few checks guards against such early
+ * stops.  The count of passes so far is kept between glbm_step calls and
+ * cleared with the history (set_medium, set_force, init_equilibrium).
+ * EINVAL unless 1 <= patience <= 1e6.
+ */
+glbm_status glbm_set_convergence(glbm_t h, int patience);
+
 /* Mean velocity (Ux, Uy) of the last completed step; waits for the stream.
  * ESTATE before the first step, ENAN if it is not finite. */
 glbm_status glbm_mean_velocity(glbm_t h, double out[2]);

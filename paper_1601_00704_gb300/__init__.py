@@ -35,6 +35,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
            "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
+           "glbm_set_convergence",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -86,6 +87,7 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_destroy": ([h], None),
         "glbm_debug_fail_launch": ([ll], None),
         "glbm_save": ([h, C.c_char_p], i),
+        "glbm_set_convergence": ([h, i], i),
         "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),
         "glbm_step_reduce_noalloc": ([_VP, _VP, _VP, _VP, _VP, i, i, ll, d, d, d,
@@ -246,6 +248,10 @@ class Solver:
             raise ValueError("mixing host and device arrays")
         self._check(self._lib.glbm_init_equilibrium(
             self._h, args[0].ptr, args[1].ptr, args[2].ptr, int(dev == {True})))
+
+    def set_convergence(self, patience):
+        """Converge only after `patience` consecutive passing checks."""
+        self._check(self._lib.glbm_set_convergence(self._h, int(patience)))
 
     def step(self, n, tol=0.0, check_every=100):
         done, conv = C.c_longlong(), C.c_int()

@@ -69,6 +69,7 @@ struct glbm {
     bool sr = true;           // 16-bit storage: stochastic rounding
     bool at_rest = false;     // state is f_eq(1, 0) (zero deviations)
     uint32_t seed = 0x2545F491u;
+    int patience = 1;         // consecutive passing checks for convergence
     long long tstep = 0;      // time steps launched since the last reset
     long long steps = 0, launches = 0;
     // 16-bit storage: device copy of tstep, read by the step kernels of
@@ -80,7 +81,7 @@ struct glbm {
     struct Graph {
         int parity;
         long long chunk;
-        int reduce, test;
+        int reduce, test, patience;
         double tol, scale;
         cudaGraphExec_t exec;
     };
@@ -210,7 +211,7 @@ int nparts(const glbm *h) {
 glbm_status finalize(glbm *h, double tol) {
     if (injected_failure()) return fail(h, GLBM_ECUDA, "finalize launch: injected failure (test hook)");
     k_finalize<<<1, 256, 0, h->stream>>>(h->partial, nparts(h), 1.0 / double(h->N), tol, h->dstat,
-                                         h->elem == 2 ? h->pmax : nullptr);
+                                         h->elem == 2 ? h->pmax : nullptr, h->patience);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(h, GLBM_ECUDA, "finalize launch: %s", cudaGetErrorString(e));
     h->launches++;
@@ -258,7 +259,7 @@ glbm_status run_chunk(glbm *h, long long chunk, bool reduce, double tol) {
         for (int i = 0; i < h->ngraphs; ++i) {
             const glbm::Graph &g = h->graphs[i];
             if (g.parity == h->cur && g.chunk == chunk && g.reduce == int(reduce) && g.test == test &&
-                g.tol == tol && g.scale == h->scale) {
+                g.tol == tol && g.scale == h->scale && g.patience == h->patience) {
                 CU(h, cudaGraphLaunch(g.exec, h->stream));
                 h->launches += chunk + (reduce ? 1 : 0) + (small ? 1 : 0);
                 h->tstep += chunk;
@@ -295,7 +296,7 @@ glbm_status run_chunk(glbm *h, long long chunk, bool reduce, double tol) {
             h->reduced = r0;
             return st;
         }
-        h->graphs[h->ngraphs++] = {p0, chunk, int(reduce), test, tol, h->scale, exec};
+        h->graphs[h->ngraphs++] = {p0, chunk, int(reduce), test, h->patience, tol, h->scale, exec};
         CU(h, cudaGraphLaunch(exec, h->stream));
         return GLBM_OK;
     }
@@ -650,6 +651,14 @@ glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every, long l
     return GLBM_OK;
 }
 
+glbm_status glbm_set_convergence(glbm_t h, int patience) {
+    if (glbm_status s = check(h)) return s;
+    if (patience < 1 || patience > 1000000)
+        return fail(h, GLBM_EINVAL, "set_convergence: patience must be in [1, 1e6] (got %d)", patience);
+    h->patience = patience;
+    return GLBM_OK;
+}
+
 glbm_status glbm_mean_velocity(glbm_t h, double out[2]) {
     if (glbm_status s = check(h)) return s;
     if (!out) return fail(h, GLBM_EINVAL, "mean_velocity: out is NULL");
@@ -751,7 +760,8 @@ struct CkptHeader {
     unsigned flags;
     int forch, at_rest, reduced, sr;
     double tau, feps_mode, gx, gy, scale;
-    unsigned seed, pad;
+    unsigned seed;
+    int patience;
     long long tstep, steps;
     DevStatus status;
     unsigned long long checksum;
@@ -804,6 +814,7 @@ glbm_status glbm_save(glbm_t h, const char *path) {
     hd.gy = h->gy;
     hd.scale = h->scale;
     hd.seed = h->seed;
+    hd.patience = h->patience;
     hd.tstep = h->tstep;
     hd.steps = h->steps;
     CU(h, cudaMemcpy2DAsync(buf.data(), N * h->elem, h->buf[h->cur], size_t(h->plane) * h->elem, N * h->elem, 9,
@@ -869,6 +880,7 @@ glbm_status glbm_load(glbm_t h, const char *path) {
     h->gy = hd.gy;
     h->scale = hd.scale;
     h->seed = hd.seed;
+    h->patience = hd.patience >= 1 ? hd.patience : 1;
     h->tstep = hd.tstep;
     h->steps = hd.steps;
     h->has_medium = true;

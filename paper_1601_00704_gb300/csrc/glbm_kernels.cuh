@@ -734,12 +734,16 @@ struct DevStatus {
     int converged;     // set by the last finalize
     int nonfinite;     // mean velocity not finite
     float gmax;        // 16-bit storage: largest stored |g*S| at that step
+    int streak;        // consecutive checks that passed the relative-change test
+    int pad;
 };
 
 // K3 finalize: fixed-order FP64 sum of the block partials, mean, test.
+// Converged once `patience` consecutive checks pass |Ux - Ux_prev| <=
+// tol |Ux| (patience 1: the first pass).
 __global__ void __launch_bounds__(256)
 k_finalize(const double *__restrict__ partial, int nparts, double inv_n, double tol,
-           DevStatus *__restrict__ st, const float *__restrict__ pmax) {
+           DevStatus *__restrict__ st, const float *__restrict__ pmax, int patience = 1) {
     __shared__ double sh[2][256];
     double a = 0.0, b = 0.0;
     float m = 0.0f;
@@ -765,8 +769,9 @@ k_finalize(const double *__restrict__ partial, int nparts, double inv_n, double 
         st->uy = uy;
         const bool fin = isfinite(ux) && isfinite(uy);
         st->nonfinite = fin ? 0 : 1;
-        st->converged = (fin && tol > 0.0 && st->have_prev &&
-                         fabs(ux - st->prev_ux) <= tol * fabs(ux)) ? 1 : 0;
+        const bool pass = fin && tol > 0.0 && st->have_prev && fabs(ux - st->prev_ux) <= tol * fabs(ux);
+        st->streak = pass ? st->streak + 1 : 0;
+        st->converged = st->streak >= patience ? 1 : 0;
         st->prev_ux = ux;
         st->have_prev = 1;
         st->gmax = m;

@@ -140,3 +140,74 @@ def test_kapp_field_matches_oracle(pkg, orc):
         orc.qsat_from_langmuir_volume(0.005, 1.65e3, 0.04, 0.2, 0.717), rel=1e-15)
     with pytest.raises(pkg.GLBMError):
         pkg.kapp_field(np.zeros(4), np.zeros(4, bool), np.full(4, 0.02), *args)
+
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+BF16_ULP = 2.0 ** -7
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("walls", [True, False])
+def test_batch_matches_oracle_elementwise(pkg, orc, storage, walls):
+    """Every medium of an uneven batch against the FP64 oracle, element by
+    element, after 1, 4 and 10 steps: FP32 within the step tolerance of the
+    single-lattice parity suite (|df| <= 1e-6 * n * max|g|), BF16 within one
+    stochastic rounding (2^-7 relative) per step and population."""
+    shapes = [(48, 64), (32, 128), (80, 36), (17, 516)]
+    md = media_for(shapes, seed=31)
+    b = pkg.Batch(shapes, tau=0.8, storage=storage, walls=walls)
+    for i, (eps, K) in enumerate(md):
+        b.set_medium(i, eps, K)
+    b.set_force(3e-4, -1e-4)
+    orcs = []
+    for (ny, nx), (eps, K) in zip(shapes, md):
+        o = orc.Oracle(nx, ny, tau=0.8, periodic_y=not walls)
+        o.set_medium(eps, K)
+        o.set_force(3e-4, -1e-4)
+        orcs.append(o)
+    done = 0
+    for n in (1, 3, 6):
+        b.step(n, check_every=n)
+        done += n
+        res = b.results()
+        for i, o in enumerate(orcs):
+            o.step(n)
+            gmax = np.abs(o.f - W[:, None, None]).max()
+            tol = (1e-6 if storage == "f32" else 2 * BF16_ULP) * done * gmax
+            np.testing.assert_allclose(b.distributions(i), o.f, rtol=0, atol=tol, err_msg=f"medium {i}")
+            uref = o.mean_u[0]
+            assert abs(res["mean_u"][i][0] - uref) <= (2e-5 if storage == "f32" else 3e-2) * done * abs(uref) + 1e-15
+
+
+def test_batch_converges_per_medium_like_the_oracle(pkg, orc):
+    """Clear channels (eps = 1, K = inf, walls in y) of three widths plus a
+    uniform Darcy medium, run with a convergence test until each medium
+    leaves the batch on its own: each converged K_app equals the converged
+    FP64 oracle's within the FP32 bound 1e-4, narrow channels leave first,
+    and the Darcy medium gives K G / nu exactly (K_app = K)."""
+    shapes = [(8, 32), (16, 32), (24, 32), (12, 16)]
+    b = pkg.Batch(shapes, storage="f32")
+    inputs = []
+    for i, (ny, nx) in enumerate(shapes):
+        if i < 3:
+            eps, K = np.ones((ny, nx)), np.full((ny, nx), np.inf)
+        else:
+            eps, K = media.uniform_medium(nx, ny, 0.4, 2e-2)
+        b.set_medium(i, eps, K)
+        inputs.append((eps, K))
+    b.set_force(1e-6)
+    done, left = b.step(200000, tol=1e-10, check_every=100)
+    assert left == 0
+    res = b.results()
+    assert res["converged"].all()
+    steps = res["steps"]
+    assert steps[0] < steps[1] < steps[2]
+    for i, ((ny, nx), (eps, K)) in enumerate(zip(shapes, inputs)):
+        o = orc.Oracle(nx, ny)
+        o.set_medium(eps, K)
+        o.set_force(1e-6)
+        o.step(200000, tol=1e-10, check_every=100)
+        assert res["kxx"][i] == pytest.approx(o.permeability(), rel=1e-4), i
+    # uniform porous medium with walls: Brinkman layers at the walls, Darcy
+    # value 2e-2 in the core; the mean lies just below it
+    assert 0.8 * 2e-2 < res["kxx"][3] < 2e-2
