@@ -288,9 +288,20 @@ glbm_status glbm_batch_reset(glbm_batch_t b);
  * media alternating). */
 glbm_status glbm_batch_set_schedule(glbm_batch_t b, int threads, int order);
 
-/* Time every schedule for 2 x trial_steps steps on this batch, keep the
- * fastest (returned in threads/order, either may be NULL) and reset the batch
- * (the trials advance it).  Requires every medium set. */
+/* Persistent variant (on != 0): each chunk of glbm_batch_step is ONE
+ * cooperative launch in which the blocks loop over the tile table for every
+ * time step and meet at a grid-wide barrier between steps (every wait is
+ * bounded, about a second, after which the call returns ECUDA instead of
+ * hanging); off (default): one launch per time step, chunks replayed from
+ * captured CUDA graphs.  Both give the same bits.  The autotuner tries both.
+ * glbm_batch_get_persistent reports the current choice. */
+glbm_status glbm_batch_set_persistent(glbm_batch_t b, int on);
+glbm_status glbm_batch_get_persistent(glbm_batch_t b, int *on);
+
+/* Time every schedule (threads x order x persistent or not) for
+ * 2 x trial_steps steps on this batch, keep the fastest (threads/order
+ * returned, either may be NULL; see glbm_batch_get_persistent) and reset
+ * the batch (the trials advance it).  Requires every medium set. */
 glbm_status glbm_batch_autotune(glbm_batch_t b, int trial_steps, int *threads,
                                 int *order);
 

@@ -35,7 +35,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
            "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
-           "glbm_set_convergence",
+           "glbm_set_convergence", "glbm_batch_set_persistent", "glbm_batch_get_persistent",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -88,6 +88,8 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_debug_fail_launch": ([ll], None),
         "glbm_save": ([h, C.c_char_p], i),
         "glbm_set_convergence": ([h, i], i),
+        "glbm_batch_set_persistent": ([h, i], i),
+        "glbm_batch_get_persistent": ([h, C.POINTER(i)], i),
         "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),
         "glbm_step_reduce_noalloc": ([_VP, _VP, _VP, _VP, _VP, i, i, ll, d, d, d,
@@ -355,6 +357,17 @@ class Batch:
 
     def set_schedule(self, threads, order):
         self._check(self._lib.glbm_batch_set_schedule(self._h, int(threads), int(order)))
+
+    def set_persistent(self, on=True):
+        """One cooperative launch per chunk with grid barriers between steps
+        (True) or one launch per step from captured graphs (False)."""
+        self._check(self._lib.glbm_batch_set_persistent(self._h, int(bool(on))))
+
+    @property
+    def persistent(self):
+        v = C.c_int()
+        self._check(self._lib.glbm_batch_get_persistent(self._h, C.byref(v)))
+        return bool(v.value)
 
     def autotune(self, trial_steps=20):
         t, o = C.c_int(), C.c_int()

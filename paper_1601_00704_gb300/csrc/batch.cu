@@ -96,6 +96,99 @@ k_batch_step(const T *__restrict__ src_all, T *__restrict__ dst_all,
     }
 }
 
+// Grid-wide barrier of the persistent kernel (all blocks co-resident: the
+// launch is cooperative).  Generation counting: the last block to arrive
+// resets the count and bumps the generation; the others wait for the bump,
+// at most kBarrierCycles (~1 s), after which they record a timeout in *err
+// and give up.  Returns false once this block has given up.
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+constexpr long long kBarrierCycles = 2ll << 30;
+
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &bar->gen;
+        const unsigned g = *gen;
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            bar->count = 0u;
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Persistent variant of k_batch_step: one cooperative launch runs `nsteps`
+// time steps of every tile, the blocks striding over the tile table and
+// meeting at a grid barrier between steps.  Step s reads buffer
+// (parity0 + s) & 1 and writes the other; the last step writes the per-tile
+// partials.  Loads of the distributions go through L2 only (they were
+// written by other blocks of this launch).  The stochastic-rounding key of
+// step s is that of step clock->step + s, and the last block to finish
+// advances clock->step by nsteps.
+template <typename T, int THREADS, bool WALLS>
+__global__ void __launch_bounds__(THREADS, kMinBlocks<T> * 128 / THREADS)
+k_batch_persist(T *__restrict__ buf0, T *__restrict__ buf1, int parity0, int nsteps,
+                const typename Store<T>::R *__restrict__ alpha, const typename Store<T>::R *__restrict__ epsv,
+                const BTile *__restrict__ tiles, int ntiles, const BMed *__restrict__ meds,
+                Phys<typename Store<T>::R> ph, StepClock *__restrict__ clock, double *__restrict__ partial,
+                GridBar *__restrict__ bar, int *__restrict__ err) {
+    constexpr int VEC = kVecOf<T>;
+    const unsigned step0 = clock->step, seed = clock->seed;
+    for (int s = 0; s < nsteps; ++s) {
+        const bool last = s == nsteps - 1;
+        const T *src = ((parity0 + s) & 1) ? buf1 : buf0;
+        T *dst = ((parity0 + s) & 1) ? buf0 : buf1;
+        if (Store<T>::kSmall) ph.step_key = step_key_of(step0 + unsigned(s), seed);
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const BTile tl = tiles[t];
+            const BMed m = meds[tl.med];
+            Geo geo;
+            geo.nx = m.nx;
+            geo.ny = m.ny;
+            geo.plane = m.plane;
+            geo.bpr = m.bpr;
+            const int x0 = (tl.bx * THREADS + threadIdx.x) * VEC;
+            double sx = 0.0, sy = 0.0;
+            float gm = 0.0f;
+            if (last) {
+                step_body<T, VEC, WALLS, false, true, true>(src + m.off_f, dst + m.off_f, alpha + m.off_c,
+                                                            epsv + m.off_c, nullptr, geo, ph, x0, tl.y, sx, sy, gm);
+                block_sum2(sx, sy);
+                if (threadIdx.x == 0) {
+                    partial[2ll * t] = sx;
+                    partial[2ll * t + 1] = sy;
+                }
+                __syncthreads();  // block_sum2's shared slots are reused by the next tile
+            } else {
+                step_body<T, VEC, WALLS, false, false, true>(src + m.off_f, dst + m.off_f, alpha + m.off_c,
+                                                             epsv + m.off_c, nullptr, geo, ph, x0, tl.y, sx, sy,
+                                                             gm);
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) clock->step = step0 + unsigned(nsteps);
+}
+
 // Per-medium finalize: block j reduces active medium act[j] over its tiles.
 __global__ void __launch_bounds__(256)
 k_batch_finalize(const double *__restrict__ partial, const BMed *__restrict__ meds, const int *__restrict__ act,
@@ -195,6 +288,10 @@ struct glbm_batch {
     bool reduced = false;
     double gx = 0.0, gy = 0.0;
     int threads = 128, order = 0;
+    bool persistent = false;  // one cooperative launch per chunk (k_batch_persist)
+    GridBar *dbar = nullptr;
+    int *derr = nullptr;      // persistent kernel: grid-barrier timeout flag
+    int nsm = 0;
     struct Graph {
         int parity, chunk, test;
         cudaGraphExec_t exec;
@@ -328,11 +425,65 @@ cudaError_t launch_bstep(glbm_batch *h, bool reduce) {
     return launch_bstep_s<float>(h, reduce);
 }
 
+template <typename T, int THREADS, bool WALLS>
+cudaError_t launch_persist_t(glbm_batch *h, int chunk) {
+    using R = typename Store<T>::R;
+    Phys<R> ph;
+    ph.omega = R(1.0 / h->tau);
+    ph.A = R(1.0 - 0.5 / h->tau);
+    ph.gx = R(h->gx);
+    ph.gy = R(h->gy);
+    ph.scale = R(1);
+    ph.inv_scale = R(1);
+    ph.step_key = 0;
+    ph.sr = 1;
+    auto kern = k_batch_persist<T, THREADS, WALLS>;
+    int per_sm = 0;
+    if (cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0)) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = int(std::min<long long>(h->ntiles, (long long)per_sm * h->nsm));
+    if (glbm_injected_failure()) return cudaErrorLaunchFailure;  // test hook: nothing is launched
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(THREADS);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<T *>(h->buf[0]), static_cast<T *>(h->buf[1]),
+                                       h->parity, chunk, static_cast<const R *>(h->coef[0]),
+                                       static_cast<const R *>(h->coef[1]), static_cast<const BTile *>(h->dtiles),
+                                       h->ntiles, static_cast<const BMed *>(h->dmed), ph, h->dclock, h->partial,
+                                       h->dbar, h->derr);
+    if (e != cudaSuccess) return e;
+    h->launches++;
+    if (chunk % 2) h->parity ^= 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_persist_s(glbm_batch *h, int chunk) {
+    const bool walls = !(h->flags & GLBM_PERIODIC_Y);
+    switch (h->threads) {
+        case 64: return walls ? launch_persist_t<T, 64, true>(h, chunk) : launch_persist_t<T, 64, false>(h, chunk);
+        case 256: return walls ? launch_persist_t<T, 256, true>(h, chunk) : launch_persist_t<T, 256, false>(h, chunk);
+        default: return walls ? launch_persist_t<T, 128, true>(h, chunk) : launch_persist_t<T, 128, false>(h, chunk);
+    }
+}
+
 // Enqueue `chunk` steps (+ the per-medium reduction at the last one); the
 // first failed launch stops it and is returned.
 cudaError_t enqueue_chunk(glbm_batch *h, int chunk, double tol) {
-    for (int s = 0; s < chunk; ++s)
-        if (cudaError_t e = launch_bstep(h, s == chunk - 1)) return e;
+    if (h->persistent) {
+        const cudaError_t e = h->storage == GLBM_BF16DEV ? launch_persist_s<__nv_bfloat16>(h, chunk)
+                                                         : launch_persist_s<float>(h, chunk);
+        if (e != cudaSuccess) return e;
+    } else {
+        for (int s = 0; s < chunk; ++s)
+            if (cudaError_t e = launch_bstep(h, s == chunk - 1)) return e;
+    }
     if (glbm_injected_failure()) return cudaErrorLaunchFailure;
     k_batch_finalize<<<h->nact, 256, 0, h->stream>>>(h->partial, h->dmed, h->dact, tol, h->dstat);
     if (cudaError_t e = cudaGetLastError()) return e;
@@ -341,9 +492,22 @@ cudaError_t enqueue_chunk(glbm_batch *h, int chunk, double tol) {
 }
 
 // Run one chunk, from a captured graph when the same (parity, length, test)
-// chunk has been seen since the table last changed.
+// chunk has been seen since the table last changed.  The persistent kernel
+// is one launch per chunk already and runs uncaptured.
 glbm_status run_chunk(glbm_batch *h, int chunk, double tol) {
     const int test = tol > 0.0;
+    if (h->persistent) {
+        const int p0 = h->parity;
+        const long long l0 = h->launches;
+        if (cudaError_t e = enqueue_chunk(h, chunk, tol)) {
+            (void)cudaGetLastError();
+            h->parity = p0;
+            h->launches = l0;
+            return bfail(h, GLBM_ECUDA, "batch: persistent step launch failed: %s%s", cudaGetErrorString(e),
+                         e == cudaErrorLaunchFailure ? " (injected by the test hook)" : "");
+        }
+        return GLBM_OK;
+    }
     for (auto &g : h->graphs) {
         if (g.parity == h->parity && g.chunk == chunk && g.test == test) {
             BCU(h, cudaGraphLaunch(g.exec, h->stream));
@@ -394,7 +558,7 @@ void brelease(glbm_batch *h) {
     drop_graphs(h);
     for (auto &p : h->buf) if (p) cudaFree(p), p = nullptr;
     for (auto &p : h->coef) if (p) cudaFree(p), p = nullptr;
-    void *ptrs[] = {h->dmed, h->dtiles, h->dact, h->partial, h->dstat, h->dclock, h->dflag, h->stage};
+    void *ptrs[] = {h->dmed, h->dtiles, h->dact, h->partial, h->dstat, h->dclock, h->dflag, h->stage, h->dbar, h->derr};
     for (void *p : ptrs) if (p) cudaFree(p);
     h->dmed = nullptr;
     h->dtiles = nullptr;
@@ -404,6 +568,8 @@ void brelease(glbm_batch *h) {
     h->dclock = nullptr;
     h->dflag = nullptr;
     h->stage = nullptr;
+    h->dbar = nullptr;
+    h->derr = nullptr;
     if (h->hstat) cudaFreeHost(h->hstat), h->hstat = nullptr;
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream), h->stream = nullptr;
 }
@@ -492,6 +658,11 @@ glbm_status glbm_batch_create(int count, const int *nx, const int *ny, double ta
     if (e == cudaSuccess) e = cudaMalloc(&h->dstat, sizeof(DevStatus) * count);
     if (e == cudaSuccess) e = cudaMalloc(&h->dclock, sizeof(StepClock));
     if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, sizeof(GridBar));
+    if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dbar, 0, sizeof(GridBar), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
     if (e == cudaSuccess) e = cudaMallocHost(&h->hstat, sizeof(DevStatus) * count);
     glbm_status s = GLBM_OK;
     if (e != cudaSuccess)
@@ -569,6 +740,19 @@ glbm_status glbm_batch_set_schedule(glbm_batch_t h, int threads, int order) {
     return build_table(h);
 }
 
+glbm_status glbm_batch_set_persistent(glbm_batch_t h, int on) {
+    if (glbm_status s = bcheck(h)) return s;
+    h->persistent = on != 0;
+    drop_graphs(h);
+    return GLBM_OK;
+}
+
+glbm_status glbm_batch_get_persistent(glbm_batch_t h, int *on) {
+    if (!h || !on) return GLBM_EINVAL;
+    *on = h->persistent ? 1 : 0;
+    return GLBM_OK;
+}
+
 glbm_status glbm_batch_step(glbm_batch_t h, long long n, double tol, int check_every, long long *steps_done,
                             int *active_left) {
     if (steps_done) *steps_done = 0;
@@ -608,6 +792,16 @@ glbm_status glbm_batch_step(glbm_batch_t h, long long n, double tol, int check_e
             h->parity_of[m] = h->parity;
             h->steps_of[m] = h->tstep;
         }
+    if (h->persistent) {
+        int berr = 0;
+        BCU(h, cudaMemcpyAsync(&berr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        BCU(h, cudaStreamSynchronize(h->stream));
+        if (berr) {
+            BCU(h, cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream));
+            BCU(h, cudaMemsetAsync(h->dbar, 0, sizeof(GridBar), h->stream));
+            return bfail(h, GLBM_ECUDA, "batch_step: a grid barrier of the persistent kernel timed out");
+        }
+    }
     if (steps_done) *steps_done = done;
     if (active_left) *active_left = h->nact;
     BCU(h, cudaGetLastError());
@@ -624,11 +818,14 @@ glbm_status glbm_batch_autotune(glbm_batch_t h, int trial_steps, int *threads, i
     BCU(h, cudaEventCreate(&e1));
     float best = 1e30f;
     int bt = 128, bo = 0;
+    bool bp = false;
     const int cand_t[3] = {64, 128, 256};
+    for (int pers = 0; pers < 2; ++pers)
     for (int o = 0; o < 3; ++o)
         for (int t : cand_t) {
             h->threads = t;
             h->order = o;
+            h->persistent = pers != 0;
             if (glbm_status s = build_table(h)) return s;
             if (glbm_status s = run_chunk(h, trial_steps, 0.0)) return s;  // capture + warm-up
             BCU(h, cudaEventRecord(e0, h->stream));
@@ -642,12 +839,14 @@ glbm_status glbm_batch_autotune(glbm_batch_t h, int trial_steps, int *threads, i
                 best = ms;
                 bt = t;
                 bo = o;
+                bp = pers != 0;
             }
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->threads = bt;
     h->order = bo;
+    h->persistent = bp;
     if (threads) *threads = bt;
     if (order) *order = bo;
     return zero_state(h);  // trials advanced the state: start again from rest

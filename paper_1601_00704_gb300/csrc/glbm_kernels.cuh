@@ -208,20 +208,38 @@ struct Geo {
     int bpr;          // blocks per row
 };
 
-// Vector moves of 8 bytes or a multiple of 16 bytes.
-template <typename X, int N>
+// Vector moves of 8 bytes or a multiple of 16 bytes.  CG: load through L2
+// only (ld.global.cg), for data that other blocks of the same launch wrote
+// (the persistent batch kernel), which a non-coherent L1 line could hide.
+template <typename X, int N, bool CG = false>
 __device__ __forceinline__ void ld16(const X *__restrict__ p, X (&out)[N]) {
     constexpr int B = int(N * sizeof(X));
     static_assert(B == 8 || B % 16 == 0, "8-byte or 16-byte multiple");
     if constexpr (B == 8) {
-        uint2 u = *reinterpret_cast<const uint2 *>(p);
+        uint2 u = CG ? __ldcg(reinterpret_cast<const uint2 *>(p)) : *reinterpret_cast<const uint2 *>(p);
         memcpy(&out[0], &u, 8);
     } else {
 #pragma unroll
         for (int j = 0; j < B / 16; ++j) {
-            uint4 u = reinterpret_cast<const uint4 *>(p)[j];
+            uint4 u = CG ? __ldcg(reinterpret_cast<const uint4 *>(p) + j) : reinterpret_cast<const uint4 *>(p)[j];
             memcpy(&out[j * (16 / sizeof(X))], &u, 16);
         }
+    }
+}
+// One element, optionally through L2 only (see ld16).
+template <bool CG, typename X>
+__device__ __forceinline__ X ld1(const X *p) {
+    if constexpr (CG) {
+        if constexpr (sizeof(X) == 2) {
+            const unsigned short u = __ldcg(reinterpret_cast<const unsigned short *>(p));
+            X v;
+            memcpy(&v, &u, 2);
+            return v;
+        } else {
+            return __ldcg(p);
+        }
+    } else {
+        return *p;
     }
 }
 template <typename X, int N>
@@ -414,7 +432,7 @@ __device__ __forceinline__ void load_coef(const R *__restrict__ p, R (&c)[VEC]) 
 // INTERIOR: 0 < y < ny-1, so no population crosses a wall or the periodic
 // y boundary and every shift mode is a compile-time constant.  x0 must be a
 // valid node (callers clamp idle threads to x0 = 0 and discard their result).
-template <typename T, int VEC, bool WALLS, bool INTERIOR, bool FORCH>
+template <typename T, int VEC, bool WALLS, bool INTERIOR, bool FORCH, bool CG = false>
 __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo, int x0, int y,
                                        int lane, typename Store<T>::R inv_s,
                                        const typename Store<T>::R *__restrict__ alpha,
@@ -441,7 +459,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
                     // halfway bounce-back: the opposite population that left
                     // this node towards the wall returns reversed
                     p = src + (long long)opp(i) * geo.plane + (long long)y * nx + x0;
-                    g[0][i] = Store<T>::ld(*p, inv_s);
+                    g[0][i] = Store<T>::ld(ld1<CG>(p), inv_s);
                     continue;
                 }
                 ys = ys < 0 ? ys + ny : ys - ny;
@@ -449,7 +467,7 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
             int xs = x0 - cx(i);
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             p = src + (long long)i * geo.plane + (long long)ys * nx + xs;
-            g[0][i] = Store<T>::ld(*p, inv_s);
+            g[0][i] = Store<T>::ld(ld1<CG>(p), inv_s);
         }
     } else {
         // shift mode per population: 0 none, +1 take x-1, -1 take x+1;
@@ -476,10 +494,10 @@ __device__ __forceinline__ void gather(const T *__restrict__ src, const Geo &geo
                 }
             }
             const T *row = src + (long long)pl * geo.plane + (long long)ys * nx;
-            ld16<T, VEC>(row + x0, v[i]);
+            ld16<T, VEC, CG>(row + x0, v[i]);
             edge[i] = T(0);
-            if (mode[i] == 1 && first) edge[i] = row[xl];
-            if (mode[i] == -1 && last) edge[i] = row[xr];
+            if (mode[i] == 1 && first) edge[i] = ld1<CG>(row + xl);
+            if (mode[i] == -1 && last) edge[i] = ld1<CG>(row + xr);
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -552,7 +570,7 @@ __device__ __forceinline__ float block_max(float m) {
 // (src/dst/coefficients point at that lattice's plane 0).  Adds this thread's
 // FP64 velocity sums to sx, sy and, for 16-bit storage, the largest stored
 // magnitude to gm.
-template <typename T, int VEC, bool WALLS, bool FORCH, bool REDUCE>
+template <typename T, int VEC, bool WALLS, bool FORCH, bool REDUCE, bool CG = false>
 __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restrict__ dst,
                                           const typename Store<T>::R *__restrict__ alpha,
                                           const typename Store<T>::R *__restrict__ epsv,
@@ -567,9 +585,11 @@ __device__ __forceinline__ void step_body(const T *__restrict__ src, T *__restri
 
     R g[VEC][9], a[VEC], e[VEC], b[VEC];
     if (y > 0 && y < geo.ny - 1)
-        gather<T, VEC, WALLS, true, FORCH>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e, b);
+        gather<T, VEC, WALLS, true, FORCH, CG>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e,
+                                               b);
     else
-        gather<T, VEC, WALLS, false, FORCH>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e, b);
+        gather<T, VEC, WALLS, false, FORCH, CG>(src, geo, x0, y, lane, ph.inv_scale, alpha, epsv, betav, n0, g, a, e,
+                                                b);
 
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {

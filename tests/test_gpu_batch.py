@@ -211,3 +211,31 @@ def test_batch_converges_per_medium_like_the_oracle(pkg, orc):
     # uniform porous medium with walls: Brinkman layers at the walls, Darcy
     # value 2e-2 in the core; the mean lies just below it
     assert 0.8 * 2e-2 < res["kxx"][3] < 2e-2
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("walls", [True, False])
+@pytest.mark.parametrize("threads", [64, 256])
+def test_persistent_matches_graph_launches(pkg, storage, walls, threads):
+    """The persistent variant (one cooperative launch per chunk, grid
+    barriers between steps) gives the same bits as one launch per step, over
+    odd chunk lengths and a convergence test that removes media mid-run."""
+    shapes = SHAPES + [(8, 16), (12, 8)]
+    md = media_for(shapes, seed=44)
+    outs = []
+    for pers in (False, True):
+        b = pkg.Batch(shapes, tau=0.8, storage=storage, walls=walls)
+        for i, (eps, K) in enumerate(md):
+            b.set_medium(i, eps, K)
+        b.set_schedule(threads, 0)
+        b.set_persistent(pers)
+        assert b.persistent == pers
+        b.set_force(2e-5, -5e-6)
+        b.step(37, check_every=10)
+        b.step(400, tol=1e-4, check_every=25)
+        res = b.results()
+        outs.append(([b.distributions(i) for i in range(len(shapes))], res))
+    for a, c in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(a, c)
+    for k in ("kxx", "steps", "converged"):
+        assert np.array_equal(outs[0][1][k], outs[1][1][k])
