@@ -276,6 +276,10 @@ glbm_status glbm_batch_create(int count, const int *nx, const int *ny,
 glbm_status glbm_batch_set_medium(glbm_batch_t b, int index, const double *eps,
                                   const double *K, int device_ptrs);
 
+/* Convergence test of glbm_batch_step per medium, as glbm_set_convergence:
+ * a medium converges once `patience` consecutive checks pass (default 1). */
+glbm_status glbm_batch_set_convergence(glbm_batch_t b, int patience);
+
 /* Body force G for every medium; clears the convergence histories. */
 glbm_status glbm_batch_set_force(glbm_batch_t b, double gx, double gy);
 
@@ -482,6 +486,15 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
                             const float *bias, int cout, void *y,
                             long long ys, int relu, int f32_nchw,
                             int cout_store, int *err, void *stream);
+
+/* Choice of tensor-core convolution kernel for glbm_nn_tc_conv (process-wide):
+ * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
+ * pixels and <= 64 output channels whose weights fit shared memory run the
+ * band kernel (weights resident, each band's halo loaded once per 32-channel
+ * chunk); the rest run the tile kernel (one 128-pixel tile per CTA, one TMA
+ * tile per tap); 1 = tile kernel always; 2 = as 0 (band where it applies).
+ * Both compute the same convolution; other values reset to 0. */
+void glbm_nn_tc_set_variant(int variant);
 
 /* FP32 [cout][cin][ksize][ksize] -> BF16 [ksize^2][cout_pad][cin_pad] (the
  * padding is zero). */

@@ -36,6 +36,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
            "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
            "glbm_set_convergence", "glbm_batch_set_persistent", "glbm_batch_get_persistent",
+           "glbm_batch_set_convergence", "glbm_nn_tc_set_variant",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -89,6 +90,8 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_save": ([h, C.c_char_p], i),
         "glbm_set_convergence": ([h, i], i),
         "glbm_batch_set_persistent": ([h, i], i),
+        "glbm_batch_set_convergence": ([h, i], i),
+        "glbm_nn_tc_set_variant": ([i], None),
         "glbm_batch_get_persistent": ([h, C.POINTER(i)], i),
         "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),
@@ -357,6 +360,10 @@ class Batch:
 
     def set_schedule(self, threads, order):
         self._check(self._lib.glbm_batch_set_schedule(self._h, int(threads), int(order)))
+
+    def set_convergence(self, patience):
+        """A medium converges only after `patience` consecutive passing checks."""
+        self._check(self._lib.glbm_batch_set_convergence(self._h, int(patience)))
 
     def set_persistent(self, on=True):
         """One cooperative launch per chunk with grid barriers between steps

@@ -192,7 +192,7 @@ k_batch_persist(T *__restrict__ buf0, T *__restrict__ buf1, int parity0, int nst
 // Per-medium finalize: block j reduces active medium act[j] over its tiles.
 __global__ void __launch_bounds__(256)
 k_batch_finalize(const double *__restrict__ partial, const BMed *__restrict__ meds, const int *__restrict__ act,
-                 double tol, DevStatus *__restrict__ st) {
+                 double tol, DevStatus *__restrict__ st, int patience) {
     __shared__ double sh[2][256];
     const int m = act[blockIdx.x];
     const BMed md = meds[m];
@@ -219,7 +219,9 @@ k_batch_finalize(const double *__restrict__ partial, const BMed *__restrict__ me
         s.uy = uy;
         const bool fin = isfinite(ux) && isfinite(uy);
         s.nonfinite = fin ? 0 : 1;
-        s.converged = (fin && tol > 0.0 && s.have_prev && fabs(ux - s.prev_ux) <= tol * fabs(ux)) ? 1 : 0;
+        const bool pass = fin && tol > 0.0 && s.have_prev && fabs(ux - s.prev_ux) <= tol * fabs(ux);
+        s.streak = pass ? s.streak + 1 : 0;
+        s.converged = s.streak >= patience ? 1 : 0;
         s.prev_ux = ux;
         s.have_prev = 1;
     }
@@ -289,6 +291,7 @@ struct glbm_batch {
     double gx = 0.0, gy = 0.0;
     int threads = 128, order = 0;
     bool persistent = false;  // one cooperative launch per chunk (k_batch_persist)
+    int patience = 1;         // consecutive passing checks for a medium to converge
     GridBar *dbar = nullptr;
     int *derr = nullptr;      // persistent kernel: grid-barrier timeout flag
     int nsm = 0;
@@ -485,7 +488,7 @@ cudaError_t enqueue_chunk(glbm_batch *h, int chunk, double tol) {
             if (cudaError_t e = launch_bstep(h, s == chunk - 1)) return e;
     }
     if (glbm_injected_failure()) return cudaErrorLaunchFailure;
-    k_batch_finalize<<<h->nact, 256, 0, h->stream>>>(h->partial, h->dmed, h->dact, tol, h->dstat);
+    k_batch_finalize<<<h->nact, 256, 0, h->stream>>>(h->partial, h->dmed, h->dact, tol, h->dstat, h->patience);
     if (cudaError_t e = cudaGetLastError()) return e;
     h->launches++;
     return cudaSuccess;
@@ -744,6 +747,15 @@ glbm_status glbm_batch_set_persistent(glbm_batch_t h, int on) {
     if (glbm_status s = bcheck(h)) return s;
     h->persistent = on != 0;
     drop_graphs(h);
+    return GLBM_OK;
+}
+
+glbm_status glbm_batch_set_convergence(glbm_batch_t h, int patience) {
+    if (glbm_status s = bcheck(h)) return s;
+    if (patience < 1 || patience > 1000000)
+        return bfail(h, GLBM_EINVAL, "batch_set_convergence: patience must be in [1, 1e6] (got %d)", patience);
+    h->patience = patience;
+    drop_graphs(h);  // the finalize is captured with it
     return GLBM_OK;
 }
 

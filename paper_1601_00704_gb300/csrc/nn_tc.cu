@@ -297,6 +297,207 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     }
 }
 
+// ---- Band variant for the shallow layers ------------------------------------
+// With 32-96 input and 32-64 output channels a 128-pixel tile is only a few
+// hundred tensor-core cycles, and the tile kernel above re-reads every input
+// pixel nine times (one shifted tile per tap) through L2.  This persistent
+// variant keeps all weight slices resident in shared memory and works on
+// bands of R output rows x 128 pixels: per 32-channel chunk it loads the
+// band's halo, rows y0-1 .. y0+R of pixels x0-1 .. x0+128, ONCE, in the
+// unswizzled K-major layout
+//     [8-channel block][halo row][halo pixel][8 channels = 16 bytes],
+// where the A operand of output row r and tap (dy, dx) is a view starting
+// ((r+1+dy) * 130 + 1+dx) * 16 bytes in: core matrices of 8 pixels are 128 B
+// apart along M (SBO) and 8-channel blocks one block stride apart along K
+// (LBO).  Each band accumulates R rows into one of two TMEM buffers, so the
+// epilogue of one band overlaps the MMAs of the next.  Roles as in the tile
+// kernel: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue; every wait bounded.
+constexpr int BAND_PX = TC_M + 2;   // halo pixels per row
+constexpr int BAND_THREADS = 192;
+
+struct BandArgs {
+    int n, h, w, nchunk0, nchunk, cout, R, stages;
+    int nbx, nby;
+    long long nbands;
+    uint32_t blk_stride;   // bytes between 8-channel blocks of a stage (LBO)
+    uint32_t stage_bytes;  // 4 blocks
+    uint32_t tx_bytes;     // bytes the 4 TMA loads of a stage deliver
+    uint32_t wtile;        // bytes of one weight slice (cout rows x 64 B)
+    uint32_t acc_row;      // TMEM columns per output row (power of two >= cout)
+    uint32_t acc_cols;     // TMEM columns of one accumulator buffer (R * acc_row)
+    uint32_t tmem_cols;
+    const float *bias;
+    void *y;
+    long long ys;
+    int relu;
+    int *err;
+};
+
+// Shared-memory descriptor of an unswizzled K-major operand: core matrices
+// (8 rows x 16 B) `sbo` bytes apart along M/N and `lbo` bytes apart along K.
+__device__ __forceinline__ uint64_t sdesc_nosw(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__global__ void __launch_bounds__(BAND_THREADS, 1)
+k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+               const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int ntile_w = 9 * a.nchunk;
+    uint8_t *sW = smem;
+    uint8_t *sA = smem + size_t(ntile_w) * a.wtile;
+    constexpr int SMAX = 3;
+    __shared__ __align__(8) uint64_t full[SMAX], empty[SMAX], wfull, accfull[2], accempty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = a.stages;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&wfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], 4);  // one arrival per epilogue warp
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
+            for (int tap = 0; tap < 9; ++tap)
+                for (int ch = 0; ch < a.nchunk; ++ch)
+                    tma_load_3d(sW + size_t(tap * a.nchunk + ch) * a.wtile, &mapB, &wfull, ch * TC_KC, 0, tap);
+            long long i = 0;
+            bool go = true;
+            for (long long band = blockIdx.x; band < a.nbands && go; band += gridDim.x) {
+                const int bx = int(band % a.nbx);
+                const long long rest = band / a.nbx;
+                const int by = int(rest % a.nby), img = int(rest / a.nby);
+                const int x0 = bx * TC_M, y0 = by * a.R;
+                for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
+                    const int s = int(i % S);
+                    const long long use = i / S;
+                    if (use > 0 && !mbar_wait(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 11)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], a.tx_bytes);
+                    uint8_t *dst = sA + size_t(s) * a.stage_bytes;
+                    const bool first = ch < a.nchunk0;
+                    const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
+#pragma unroll
+                    for (int blk = 0; blk < 4; ++blk)
+                        tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
+                                    x0 - 1, y0 - 1, img);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(a.cout);
+            bool ok = mbar_wait(&wfull, 0, &abort_flag, a.err, 12);
+            tc_fence_after();
+            long long i = 0, t = 0;
+            for (long long band = blockIdx.x; band < a.nbands && ok; band += gridDim.x, ++t) {
+                const int ab = int(t & 1);
+                const long long use_ab = t >> 1;
+                if (use_ab > 0 && !mbar_wait(&accempty[ab], uint32_t(use_ab - 1) & 1u, &abort_flag, a.err, 13)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + uint32_t(ab) * a.acc_cols;
+                for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
+                    const int s = int(i % S);
+                    if (!mbar_wait(&full[s], uint32_t(i / S) & 1u, &abort_flag, a.err, 14)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(sA + size_t(s) * a.stage_bytes);
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                        const uint64_t bd = sdesc_k64(sW + size_t(tap * a.nchunk + ch) * a.wtile);
+                        for (int r = 0; r < a.R; ++r) {
+                            const uint32_t pix = uint32_t((r + 1 + dy) * BAND_PX + 1 + dx) * 16u;
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint64_t ad = sdesc_nosw(base + pix + uint32_t(2 * kk) * a.blk_stride,
+                                                               a.blk_stride, 128u);
+                                umma_bf16(acc + uint32_t(r) * a.acc_row, ad, bd + uint64_t((kk * 32) >> 4), idesc,
+                                          (ch > 0 || tap > 0 || kk > 0) ? 1u : 0u);
+                            }
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&accfull[ab]);
+            }
+        }
+    } else {
+        const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
+        long long t = 0;
+        for (long long band = blockIdx.x; band < a.nbands; band += gridDim.x, ++t) {
+            const int ab = int(t & 1);
+            if (!mbar_wait(&accfull[ab], uint32_t(t >> 1) & 1u, &abort_flag, a.err, 15)) break;
+            tc_fence_after();
+            const int bx = int(band % a.nbx);
+            const long long rest = band / a.nbx;
+            const int by = int(rest % a.nby), img = int(rest / a.nby);
+            const int px = bx * TC_M + q * 32 + lane;
+            for (int r = 0; r < a.R; ++r) {
+                const int py = by * a.R + r;
+                const bool ok = px < a.w && py < a.h;
+                const long long pixel = ((long long)img * a.h + py) * a.w + px;
+                for (int c = 0; c < a.cout; c += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + uint32_t(ab) * a.acc_cols + uint32_t(r) * a.acc_row + uint32_t(c) +
+                                  (uint32_t(q * 32) << 16),
+                              v);
+                    if (!ok) continue;
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float lo = v[2 * j] + a.bias[c + 2 * j], hi = v[2 * j + 1] + a.bias[c + 2 * j + 1];
+                        if (a.relu) {
+                            lo = fmaxf(lo, 0.0f);
+                            hi = fmaxf(hi, 0.0f);
+                        }
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+                        pk[j] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) + pixel * a.ys + c);
+                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&accempty[ab])) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
 // ---- NHWC layout kernels (memory-bound, grid-stride) --------------------------
 // One thread per pixel: coalesced reads of each input plane, cp/8 16-byte
 // stores of the pixel's padded channel vector.
@@ -446,7 +647,99 @@ bool map_act(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int tw
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// NHWC BF16 activations for the band kernel: dims (channels, w, h, n), box
+// (8 channels, 130 pixels, R + 2 rows, 1), no swizzle.
+bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int R) {
+    const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
+    const cuuint64_t strides[3] = {cuuint64_t(c) * 2, cuuint64_t(c) * 2 * w, cuuint64_t(c) * 2 * w * h};
+    const cuuint32_t box[4] = {8, cuuint32_t(BAND_PX), cuuint32_t(R + 2), 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 0 = choose per layer, 1 = tile kernel only, 2 = band kernel where it
+// applies (glbm_nn_tc_set_variant).
+int g_tc_variant = 0;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// Band kernel plan for a layer: rows per band and ring stages, or false when
+// the layer does not fit it (3x3, BF16 output, rows of >= 128 pixels,
+// cout <= 64, resident weights and two or more stages in shared memory).
+bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem) {
+    if (k != 3 || f32_nchw || w < TC_M || cout > 64) return false;
+    const size_t wbytes = size_t(9) * (cin / TC_KC) * cout * TC_KC * 2;
+    int row = 32;
+    while (row < cout) row <<= 1;
+    int r = 256 / row;  // two accumulator buffers of r rows fill at most 512 columns
+    if (r > 8) r = 8;
+    if (r > h) r = h;
+    for (; r >= 1; --r) {
+        const size_t blk = (size_t(r + 2) * BAND_PX * 16 + 127) / 128 * 128;
+        const size_t stage = 4 * blk;
+        for (int st = 3; st >= 2; --st) {
+            const size_t total = 1024 + wbytes + st * stage;
+            if (total <= kSmemLimit) {
+                *R = r;
+                *stages = st;
+                *smem = total;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
+                        const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
+                        int R, int stages, size_t smem) {
+    CUtensorMap mA0, mA1;
+    if (!map_act_band(&mA0, x0, c0, w, h, n, R) ||
+        !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, R))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: band activation tensor map rejected");
+    BandArgs a;
+    a.n = n;
+    a.h = h;
+    a.w = w;
+    a.nchunk0 = c0 / TC_KC;
+    a.nchunk = (c0 + c1) / TC_KC;
+    a.cout = cout;
+    a.R = R;
+    a.stages = stages;
+    a.nbx = (w + TC_M - 1) / TC_M;
+    a.nby = (h + R - 1) / R;
+    a.nbands = (long long)n * a.nby * a.nbx;
+    a.blk_stride = uint32_t((size_t(R + 2) * BAND_PX * 16 + 127) / 128 * 128);
+    a.stage_bytes = 4 * a.blk_stride;
+    a.tx_bytes = uint32_t(4 * (R + 2) * BAND_PX * 16);
+    a.wtile = uint32_t(cout * TC_KC * 2);
+    a.acc_row = 32;
+    while (a.acc_row < uint32_t(cout)) a.acc_row <<= 1;
+    a.acc_cols = uint32_t(R) * a.acc_row;
+    a.tmem_cols = 32;
+    while (a.tmem_cols < 2 * a.acc_cols) a.tmem_cols <<= 1;
+    a.bias = bias;
+    a.y = y;
+    a.ys = ys;
+    a.relu = relu ? 1 : 0;
+    a.err = err;
+    if (a.tmem_cols > 512) return tcfail(GLBM_EINVAL, "nn_tc_conv: band accumulators exceed tensor memory");
+    cudaError_t e = cudaFuncSetAttribute(k_tc_conv_band, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute (band)");
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: device query");
+    const long long grid = a.nbands < nsm ? a.nbands : nsm;
+    k_tc_conv_band<<<unsigned(grid), BAND_THREADS, smem, st>>>(mA0, mA1, mB, a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (band)");
+}
+
 }  // namespace
+
+extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 2) ? variant : 0; }
 
 extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, int k,
                                        const void *wt, const float *bias, int cout, void *y, long long ys, int relu,
@@ -487,6 +780,11 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return tcfail(GLBM_EINVAL, "nn_tc_conv: weight tensor map rejected");
     }
+    int R = 0, stages = 0;
+    size_t bsmem = 0;
+    if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem))
+        return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
+                           static_cast<cudaStream_t>(stream), R, stages, bsmem);
     TcConvArgs a;
     a.n = n;
     a.h = h;

@@ -200,6 +200,60 @@ def main(argv=None):
 
 
 
+# The solver's own stopping rule for timed runs, one a user can apply: the
+# relative change of the mean velocity U_x per STOP_CHECK steps at most
+# STOP_TOL on STOP_PATIENCE consecutive checks (glbm_set_convergence).  The
+# patience guards 16-bit storage, whose stochastic rounding leaves a noise
+# floor on U_x, against two checks agreeing by chance.
+STOP_TOL, STOP_CHECK, STOP_PATIENCE = 3e-6, 1000, 3
+
+
+def time_to_converged(pkg, eps, K, k_ref, storage="f32", init=None, tol=STOP_TOL, check=STOP_CHECK,
+                      patience=STOP_PATIENCE, max_steps=2_000_000):
+    """Steps and CUDA-event seconds until the solver's own convergence test
+    fires (from rest, or from init = (rho, ux, uy), the initialisation inside
+    the timing), and the error of K_app at that stop against k_ref, which
+    judges the result but plays no part in stopping."""
+    import torch
+    stream = torch.cuda.Stream()
+    s = pkg.Solver(eps.shape[1], eps.shape[0], tau=TAU, storage=storage, stream=stream)
+    torch.cuda.synchronize()
+    s.set_medium(eps, K)
+    s.set_force(G)
+    s.set_convergence(patience)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    if init is not None:
+        s.init_equilibrium(*init)
+    steps, conv = s.step(max_steps, tol=tol, check_every=check)
+    k = s.permeability()
+    e1.record(stream)
+    e1.synchronize()
+    out = {"steps": steps, "seconds": e0.elapsed_time(e1) * 1e-3, "converged": bool(conv), "k_app": k,
+           "rel_err": k / k_ref - 1}
+    s.close()
+    return out
+
+
+def reference_k(pkg, eps, K, tol=1e-8, check=10000, patience=2, max_steps=2_000_000):
+    """K_ref of a medium: FP32 from rest until U_x changes by at most tol
+    relative per `check` steps on `patience` consecutive checks."""
+    import torch
+    ref = pkg.Solver(eps.shape[1], eps.shape[0], tau=TAU, stream=torch.cuda.Stream())
+    ref.set_medium(eps, K)
+    ref.set_force(G)
+    ref.set_convergence(patience)
+    t0 = time.perf_counter()
+    steps, conv = ref.step(max_steps, tol=tol, check_every=check)
+    k = ref.permeability()
+    ref.close()
+    return k, {"steps": steps, "converged": bool(conv), "seconds": time.perf_counter() - t0,
+               "rule": f"FP32 run until U_x changes by <= {tol:g} relative per {check} steps on {patience} "
+                       f"consecutive checks"}
+
+
 def time_to_k(pkg, eps, K, k_ref, storage="f32", init=None, check=1000, crit=1e-3, max_steps=3_000_000):
     """Steps and CUDA-event seconds until |K_app/k_ref - 1| <= crit, from rest
     or from init = (rho, ux, uy) (the initialisation is inside the timing).
@@ -269,17 +323,10 @@ def _study_one(net, n, seed, ref_tol, check):
     from paper_1601_00704_gb300 import surrogate
     m = media.shale_batch(1, seed=seed, sides=(n,))[0]
     K = medium_k(pkg, m)
-    ref = pkg.Solver(n, n, tau=TAU)
-    ref.set_medium(m["eps"], K)
-    ref.set_force(G)
-    t0 = time.perf_counter()
-    ref_steps, conv = ref.step(3_000_000, tol=ref_tol, check_every=10000)
-    k_ref = ref.permeability()
-    ref_s = time.perf_counter() - t0
-    ref.close()
     # the medium is uploaded once: the solver and the network both read it
     eps_d = torch.from_numpy(np.ascontiguousarray(m["eps"], dtype=np.float64)).cuda()
     K_d = torch.from_numpy(np.ascontiguousarray(K, dtype=np.float64)).cuda()
+    k_ref, ref_info = reference_k(pkg, eps_d, K_d, tol=ref_tol)
 
     def infer(tc):
         torch.cuda.synchronize()
@@ -294,46 +341,69 @@ def _study_one(net, n, seed, ref_tol, check):
     if net.tc_error():
         raise RuntimeError("tensor-core pipeline reported a timeout")
     k_raw = NU * float(fields[1].cpu().numpy().mean()) / G
-    runs = {"cold_f32": time_to_k(pkg, eps_d, K_d, k_ref, check=check),
-            "warm_f32": time_to_k(pkg, eps_d, K_d, k_ref, init=fields, check=check),
-            "cold_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", check=check),
-            "warm_bf16": time_to_k(pkg, eps_d, K_d, k_ref, storage="bf16", init=fields, check=check)}
-    for r in ("warm_f32", "warm_bf16"):
-        runs[r]["seconds_with_inference"] = runs[r]["seconds"] + infer_s
+    variants = {"cold_f32": ("f32", None), "warm_f32": ("f32", fields),
+                "cold_bf16": ("bf16", None), "warm_bf16": ("bf16", fields)}
+    # primary: the solver's own stopping rule; K_ref only judges the answer
+    stop = {r: time_to_converged(pkg, eps_d, K_d, k_ref, storage=st, init=init)
+            for r, (st, init) in variants.items()}
+    # secondary: first check within 1e-3 of K_ref (needs K_ref in advance)
+    runs = {r: time_to_k(pkg, eps_d, K_d, k_ref, storage=st, init=init, check=check)
+            for r, (st, init) in variants.items()}
+    for d in (stop, runs):
+        for r in ("warm_f32", "warm_bf16"):
+            d[r]["seconds_with_inference"] = d[r]["seconds"] + infer_s
     base = runs["cold_f32"]["seconds"]
-    return {"seed": seed, "P_MPa": m["P"] / 1e6, "k_ref": k_ref,
-            "k_ref_from": f"FP32 cold run to relative change < {ref_tol:g} per 1e4 steps "
-                          f"({ref_steps} steps, converged={conv}, {ref_s:.1f} s)",
+    sbase = stop["cold_f32"]["seconds"]
+    return {"seed": seed, "P_MPa": m["P"] / 1e6, "k_ref": k_ref, "k_ref_from": ref_info,
             "surrogate_raw_k_app_rel_err": k_raw / k_ref - 1, "inference_s": infer_s,
-            "inference_fp32_kernels_s": infer32_s, "runs": runs,
+            "inference_fp32_kernels_s": infer32_s,
+            "stop_rule": stop,
+            "stop_rule_speedup_vs_cold_f32": {r: sbase / v.get("seconds_with_inference", v["seconds"])
+                                              for r, v in stop.items() if v["converged"] and r != "cold_f32"},
+            "runs": runs,
             "speedup_vs_cold_f32": {r: base / v.get("seconds_with_inference", v["seconds"])
                                     for r, v in runs.items() if v["met"] and r != "cold_f32"}}
 
 
-def warm_start_study(net, n=2048, seeds=(4242, 4243, 4244), ref_tol=1e-6, check=100, log=print):
-    """Cold vs surrogate-started runs on unseen n x n media of the training
-    recipe (one per seed): steps and time to |K_app/K_ref - 1| <= 1e-3 (K_ref:
-    FP32 run to relative change < ref_tol per 10^4 steps), plus the raw
-    surrogate's own K_app error.  The first seed's runs are reported in full,
-    every seed in a summary, and the median speed-ups over the seeds."""
+def _median_speedups(per, key):
+    keys = sorted({k for p in per for k in p[key]})
+    return {k: float(np.median([p[key][k] for p in per if k in p[key]])) for k in keys}
+
+
+def warm_start_study(net, n=2048, seeds=(4242, 4243, 4244), ref_tol=1e-8, check=100, log=print):
+    """Cold vs surrogate-started runs (FP32 and BF16) on unseen n x n media of
+    the training recipe, one per seed.  Primary measure: steps and time until
+    the solver's own convergence test stops the run (STOP_TOL per STOP_CHECK
+    steps on STOP_PATIENCE consecutive checks), with the error of K_app at
+    that stop against K_ref (an FP32 run to relative change <= ref_tol per
+    10^4 steps on two checks).  Secondary: steps to the first check within
+    1e-3 of K_ref (a rule that needs the answer in advance).  The first
+    seed's runs are reported in full, every seed in a summary, and the
+    median speed-ups over the seeds."""
     per = [_study_one(net, n, sd, ref_tol, check) for sd in seeds]
     first = per[0]
-    keys = sorted({k for p in per for k in p["speedup_vs_cold_f32"]})
-    med = {k: float(np.median([p["speedup_vs_cold_f32"][k] for p in per if k in p["speedup_vs_cold_f32"]]))
-           for k in keys}
     out = {"workload": f"{n}x{n} media of the training recipe, unseen seeds {list(seeds)}",
-           "criterion": f"|K_app/K_ref - 1| <= 1e-3, checked every {check} steps",
+           "stop_rule": f"relative change of U_x <= {STOP_TOL:g} per {STOP_CHECK} steps on {STOP_PATIENCE} "
+                        f"consecutive checks (the solver's own test; K_ref judges the result only)",
+           "criterion": f"secondary: first check (every {check} steps) with |K_app/K_ref - 1| <= 1e-3",
            "inference": "device-resident: features kernel, tensor-core (tcgen05) U-Net, decode kernel",
            "k_ref": first["k_ref"], "k_ref_from": first["k_ref_from"],
            "surrogate_raw_k_app_rel_err": first["surrogate_raw_k_app_rel_err"],
            "inference_s": first["inference_s"], "inference_fp32_kernels_s": first["inference_fp32_kernels_s"],
+           "stop_runs": first["stop_rule"], "stop_rule_speedup_vs_cold_f32": first["stop_rule_speedup_vs_cold_f32"],
            "runs": first["runs"], "speedup_vs_cold_f32": first["speedup_vs_cold_f32"],
            "seeds": [{"seed": p["seed"], "P_MPa": p["P_MPa"],
+                      "stop_steps": {r: v["steps"] for r, v in p["stop_rule"].items()},
+                      "stop_rel_err": {r: v["rel_err"] for r, v in p["stop_rule"].items()},
+                      "stop_converged": all(v["converged"] for v in p["stop_rule"].values()),
+                      "stop_rule_speedup_vs_cold_f32": p["stop_rule_speedup_vs_cold_f32"],
                       "steps": {r: v["steps"] for r, v in p["runs"].items()},
                       "met": all(v["met"] for v in p["runs"].values()),
                       "surrogate_raw_k_app_rel_err": p["surrogate_raw_k_app_rel_err"],
                       "speedup_vs_cold_f32": p["speedup_vs_cold_f32"]} for p in per],
-           "median_speedup_vs_cold_f32": med}
+           "median_stop_rule_speedup_vs_cold_f32": _median_speedups(per, "stop_rule_speedup_vs_cold_f32"),
+           "max_stop_rel_err": max(abs(v["rel_err"]) for p in per for v in p["stop_rule"].values()),
+           "median_speedup_vs_cold_f32": _median_speedups(per, "speedup_vs_cold_f32")}
     log(json.dumps(out))
     return out
 

@@ -47,13 +47,22 @@ CASES = [
     (1, 64, 256, 64, 0, 64, 3, True, False),    # several full 128-pixel tiles per row
     (2, 5, 130, 64, 32, 48, 3, False, False),   # one-row tiles, two input tensors, a 2-pixel last tile
     (1, 3, 384, 128, 128, 128, 3, True, False), # one-row tiles at the widest channel counts
+    # band kernel shapes (3x3, rows >= 128 pixels, cout <= 64):
+    (1, 17, 256, 64, 32, 32, 3, True, False),   # two input tensors, 3 chunks, ragged last band (8 + 8 + 1 rows)
+    (2, 16, 128, 32, 0, 32, 3, True, False),    # one pixel tile per row, two images
+    (1, 12, 300, 32, 32, 64, 3, False, False),  # 4-row bands, a 44-pixel last tile
+    (1, 8, 2048, 32, 0, 32, 3, True, False),    # one band of 8 rows across 16 pixel tiles
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 0])
 @pytest.mark.parametrize("n,h,w,c0,c1,cout,k,relu,head", CASES)
-def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head):
+def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head, variant):
+    """Every case on the tile kernel (variant 1) and with the per-layer
+    choice (variant 0: the band kernel wherever it applies)."""
     import torch
     lib = pkg.load()
+    lib.glbm_nn_tc_set_variant(variant)
     rng = np.random.default_rng(hash((n, h, w, c0, c1, cout, k)) % 2 ** 32)
     cin = c0 + c1
     x = _bf16(rng.normal(size=(n, cin, h, w)))
@@ -78,6 +87,7 @@ def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head):
         y = torch.full((n, h, w, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
     rc = lib.glbm_nn_tc_conv(_vp(x0), c0, _vp(x1) if x1 is not None else None, c1, n, h, w, k, _vp(wt),
                              _vp(bdev), cout, _vp(y), cout, int(relu), int(head), store, _vp(err), _stream())
+    lib.glbm_nn_tc_set_variant(0)
     assert rc == 0, pkg.load().glbm_last_error(None)
     torch.cuda.synchronize()
     assert int(err.item()) == 0

@@ -1,12 +1,14 @@
 """What the trained surrogate gains over the plain GLBM: on unseen media of
-its training recipe (256^2, new seeds), starting from f_eq(rho_pred, u_pred)
-reaches |K_app/K_ref - 1| <= 1e-3 in fewer steps than starting from rest,
-and both runs converge to the same K_app (the solver, not the network,
-decides the answer)."""
+its training recipe (256^2, new seeds), a run started from
+f_eq(rho_pred, u_pred) is stopped by the solver's own convergence test (the
+relative change of U_x per 1000 steps at most 3e-6 on three consecutive
+checks, a rule a user can apply without knowing the answer) after fewer
+steps than a run started from rest, and both stopped runs give K_app within
+the benchmark spec's 1e-3 of K_ref (an FP32 run to a far tighter tolerance): the
+solver, not the network, decides the answer."""
 
 import os
 
-import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -29,31 +31,40 @@ def setup():
     return pkg, T, net
 
 
-def test_warm_start_saves_steps(setup):
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_warm_start_saves_steps_under_the_stopping_rule(setup, storage):
     import media
     pkg, T, net = setup
     cold_total = warm_total = 0
     for seed in (9001, 9002, 9003, 9004):
         m = media.shale_batch(1, seed=seed, sides=(256,))[0]
         K = T.medium_k(pkg, m)
-        ref = pkg.Solver(256, 256)
-        ref.set_medium(m["eps"], K)
-        ref.set_force(T.G)
-        ref.step(2_000_000, tol=1e-7, check_every=10000)
-        k_ref = ref.permeability()
+        k_ref, _ = T.reference_k(pkg, m["eps"], K)
         pred = T.predict(net, m["eps"], K)
-        cold = T.time_to_k(pkg, m["eps"], K, k_ref)
-        warm = T.time_to_k(pkg, m["eps"], K, k_ref, init=pred)
-        assert cold["met"] and warm["met"]
+        cold = T.time_to_converged(pkg, m["eps"], K, k_ref, storage=storage)
+        warm = T.time_to_converged(pkg, m["eps"], K, k_ref, storage=storage, init=pred)
+        print(f"seed {seed} {storage}: cold {cold['steps']} steps (K err {cold['rel_err']:+.1e}), "
+              f"warm {warm['steps']} steps (K err {warm['rel_err']:+.1e})")
+        assert cold["converged"] and warm["converged"]
+        assert abs(cold["rel_err"]) <= 1e-3 and abs(warm["rel_err"]) <= 1e-3
         cold_total += cold["steps"]
         warm_total += warm["steps"]
-        print(f"seed {seed}: cold {cold['steps']} steps, warm {warm['steps']} steps")
-        # converged answers agree: the warm run continued to the same limit
-        a = pkg.Solver(256, 256)
-        a.set_medium(m["eps"], K)
-        a.set_force(T.G)
-        a.init_equilibrium(*pred)
-        a.step(2_000_000, tol=1e-7, check_every=10000)
-        assert a.permeability() == pytest.approx(k_ref, rel=2e-4)
-    print(f"total: cold {cold_total}, warm {warm_total}")
+    print(f"total {storage}: cold {cold_total}, warm {warm_total}")
     assert warm_total <= 0.5 * cold_total
+
+
+def test_warm_start_converges_to_the_same_answer(setup):
+    """Run on past the stopping rule to a tight tolerance: warm and cold
+    starts reach the same K_app."""
+    import media
+    pkg, T, net = setup
+    m = media.shale_batch(1, seed=9005, sides=(256,))[0]
+    K = T.medium_k(pkg, m)
+    k_ref, _ = T.reference_k(pkg, m["eps"], K)
+    a = pkg.Solver(256, 256)
+    a.set_medium(m["eps"], K)
+    a.set_force(T.G)
+    a.init_equilibrium(*T.predict(net, m["eps"], K))
+    a.set_convergence(2)
+    a.step(2_000_000, tol=1e-8, check_every=10000)
+    assert a.permeability() == pytest.approx(k_ref, rel=2e-5)
