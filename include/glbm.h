@@ -502,6 +502,33 @@ glbm_status glbm_nn_tc_pack_weights(const float *w, int cout, int cin,
                                     int ksize, int cout_pad, int cin_pad,
                                     void *wt, void *stream);
 
+/* Training on the tensor cores: weight gradient of a k x k convolution
+ * (zero padding k/2), dw[o][c][tap] += sum over images and pixels p of
+ * dy[p][o] * x[p + shift(tap)][c], from BF16 NHWC activations: x with cx
+ * channels (pixel stride cx, a multiple of 32; the first cin are real), dy
+ * with cy channels (a multiple of 32, <= 256; the first cout are real).  dw
+ * is FP32 [cout][cin][k][k] on the device and is accumulated into (FP32
+ * atomics: the last bits depend on the order).  FP32 accumulation of BF16
+ * products in tensor memory.  *err as in glbm_nn_tc_conv.  16-byte aligned
+ * x and dy.  EINVAL for bad sizes. */
+glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin,
+                                  const void *dy, int cy, int cout, int n,
+                                  int h, int w, int k, float *dw, int *err,
+                                  void *stream);
+
+/* Weights of the input-gradient convolution (dx = conv(dy, these)) from FP32
+ * forward weights w [cout][cin][k][k]: BF16 [k^2][cin_pad][cout_pad] with
+ * wt[tap][c][o] = w[o][c][k^2 - 1 - tap] (flipped in space, channels
+ * swapped), zero padded. */
+glbm_status glbm_nn_tc_pack_weights_flip(const float *w, int cout, int cin,
+                                         int k, int cin_pad, int cout_pad,
+                                         void *wt, void *stream);
+
+/* Bias gradient db[c] += sum over images and pixels of dy, FP32 NCHW dy with
+ * per-sample stride dybs. */
+glbm_status glbm_nn_bias_grad(const float *dy, long long dybs, int c, int n,
+                              int h, int w, float *db, void *stream);
+
 /* FP32 NCHW (n, c, h, w) -> BF16 NHWC with c_pad >= c channels (zero);
  * c_pad a multiple of 8, y 16-byte aligned. */
 glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w,

@@ -37,6 +37,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
            "glbm_set_convergence", "glbm_batch_set_persistent", "glbm_batch_get_persistent",
            "glbm_batch_set_convergence", "glbm_nn_tc_set_variant",
+           "glbm_nn_tc_conv_wgrad", "glbm_nn_tc_pack_weights_flip", "glbm_nn_bias_grad",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -92,6 +93,9 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_batch_set_persistent": ([h, i], i),
         "glbm_batch_set_convergence": ([h, i], i),
         "glbm_nn_tc_set_variant": ([i], None),
+        "glbm_nn_tc_conv_wgrad": ([_VP, i, i, _VP, i, i, i, i, i, i, _VP, _VP, _VP], i),
+        "glbm_nn_tc_pack_weights_flip": ([_VP, i, i, i, i, i, _VP, _VP], i),
+        "glbm_nn_bias_grad": ([_VP, ll, i, i, i, i, _VP, _VP], i),
         "glbm_batch_get_persistent": ([h, C.POINTER(i)], i),
         "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),

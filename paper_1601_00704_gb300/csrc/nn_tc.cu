@@ -24,140 +24,9 @@
 //  * every wait on an mbarrier is bounded: on timeout the CTA records a
 //    code in *err, stops waiting, frees its TMEM and returns.
 
-#include "glbm.h"
-
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <cstdint>
-#include <cstdio>
-#include <mutex>
-
-extern __attribute__((visibility("hidden"))) thread_local char g_create_err[512];
+#include "tc_common.cuh"
 
 namespace {
-
-constexpr int TC_M = 128;        // output pixels per tile (UMMA M)
-constexpr int TC_KC = 32;        // input channels per K step: 64-byte rows
-constexpr int TC_STAGES = 3;     // TMA ring depth (2, 3, 4 and 7-8 measured: 3 best, occupancy wins)
-constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
-constexpr int TC_STAGE_A = TC_M * TC_KC * 2;          // 8 KB
-constexpr long long kWaitCycles = 4ll << 30;          // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// ---- mbarrier ---------------------------------------------------------------
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase with the given parity.  Returns false (without
-// waiting further) once any thread of the CTA has given up.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
-            *abort_flag = 1;
-            atomicExch(err, code);
-            return false;
-        }
-    }
-    return true;
-}
-
-// ---- TMA --------------------------------------------------------------------
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
-                                            int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-        "[%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-        "[%2];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
-// ---- tcgen05 ----------------------------------------------------------------
-__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem] * B[smem]^T, BF16 inputs, FP32 accumulator.
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-            d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-// The mbarrier receives one arrival when every MMA this thread issued so far
-// has completed.
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-// Shared-memory matrix descriptor of a K-major tile whose rows are 64 bytes
-// (32 BF16) with the 64-byte swizzle, as TMA writes it: 8-row groups 512 B
-// apart (stride byte offset); the leading byte offset is unused for swizzled
-// K-major tiles; bits 46-47 hold the descriptor version 1; bits 61-63 the
-// swizzle mode (4 = 64 bytes).
-__device__ __forceinline__ uint64_t sdesc_k64(const void *tile) {
-    const uint64_t a = smem_u32(tile);
-    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((512ull >> 4) << 32) | (1ull << 46) | (4ull << 61);
-}
-// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
-// and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N/8 in bits
-// 17-22, M/16 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(TC_M >> 4) << 24);
-}
 
 struct TcConvArgs {
     int n, h, w, taps, nchunk0, nchunk, cout, tw, th;
@@ -604,38 +473,6 @@ __global__ void k_warm_decode(const float *__restrict__ y, const double *__restr
     }
 }
 
-int grid_for(long long total) {
-    long long b = (total + 255) / 256;
-    return int(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
-}
-
-glbm_status tcfail(glbm_status s, const char *msg) {
-    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
-    return s;
-}
-glbm_status tccuda(cudaError_t e, const char *what) {
-    snprintf(g_create_err, sizeof(g_create_err), "%s: %s", what, cudaGetErrorString(e));
-    return e == cudaErrorMemoryAllocation ? GLBM_ENOMEM : GLBM_ECUDA;
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encode_fn() {
-    static EncodeTiled fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(p);
-    });
-    return fn;
-}
-
 // NHWC BF16 activations: dims (channels, w, h, n), box (32, tw, th, 1).
 bool map_act(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int tw, int th) {
     const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
@@ -662,7 +499,10 @@ bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, i
 // 0 = choose per layer, 1 = tile kernel only, 2 = band kernel where it
 // applies (glbm_nn_tc_set_variant).
 int g_tc_variant = 0;
-constexpr size_t kSmemLimit = 227 * 1024;
+// dynamic shared memory budget: the 227 KB opt-in limit less room for the
+// kernels' static shared memory
+constexpr size_t kSmemLimit = 226 * 1024;
+constexpr size_t kBandMaxWeights = 80 * 1024;  // larger weight sets: tile kernel
 
 // Band kernel plan for a layer: rows per band and ring stages, or false when
 // the layer does not fit it (3x3, BF16 output, rows of >= 128 pixels,
@@ -670,6 +510,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem) {
     if (k != 3 || f32_nchw || w < TC_M || cout > 64) return false;
     const size_t wbytes = size_t(9) * (cin / TC_KC) * cout * TC_KC * 2;
+    if (wbytes > kBandMaxWeights) return false;
     int row = 32;
     while (row < cout) row <<= 1;
     int r = 256 / row;  // two accumulator buffers of r rows fill at most 512 columns

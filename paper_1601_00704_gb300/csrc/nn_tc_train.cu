@@ -1,0 +1,285 @@
+// Tensor-core (tcgen05, sm_103a) training kernels of the warm-start network:
+// the convolution weight gradient, the flipped/transposed weight packing
+// that turns the input gradient into a forward convolution on the tensor
+// cores (nn_tc.cu), and the bias gradient.  The paper has no surrogate; the
+// network is this library's own addition (see nn.cu for its FP32 kernels).
+//
+// Weight gradient of a k x k convolution (zero padding k/2):
+//     dW[o][c][tap] = sum over images and pixels p of dy[p][o] * x[p + s(tap)][c]
+// with s(tap) = (ky - k/2, kx - k/2).  As a GEMM:
+//     D[m][o] = sum_p A[m][p] * B[o][p],   m = (tap, c), o = output channel,
+// where row m of A is channel c of the input shifted by s(tap).  Both
+// operands come straight from the BF16 NHWC activations: a TMA box of 32
+// channels x 32 pixels of one row lands as 32 rows of 64 bytes (64-byte
+// swizzle), i.e. 32 consecutive channels per pixel -- an MN-major operand
+// whose 64-byte atoms (32 channels x 8 pixels) are 512 B apart along K
+// (pixels, SBO) and one box (2 KB) apart along M or N (LBO).  M = 128 rows =
+// four (tap, 32-channel chunk) boxes, each loaded at its own shift (TMA's
+// zero fill outside the image is the padding); N = the output channels (a
+// multiple of 32, one box per 32).  FP32 accumulation in TMEM.
+//
+// Each CTA takes one M tile and a contiguous range of image rows (split-K);
+// its partial sums are added to dW with FP32 atomics (so the summation order,
+// and the last bits of dW, vary from run to run).  Roles: warp 0 issues TMA,
+// warp 1 issues the MMAs and commits, warps 2-5 read the accumulator; every
+// wait is bounded as in nn_tc.cu.
+
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int WG_KP = 32;        // pixels per K step (one box row of 32 pixels)
+constexpr int WG_STAGES = 4;
+constexpr int WG_THREADS = 192;
+constexpr int WG_BOX = WG_KP * 64;  // bytes of one 32-channel x 32-pixel box
+
+struct WgradArgs {
+    int n, h, w, k, nchunk, nf;  // nf = k*k*nchunk (tap, chunk) boxes
+    int cin, cout, cy;           // real input / output channels, dy channels (multiple of 32)
+    int rows_per_cta;            // split-K: image rows (over n*h) per CTA
+    int xsteps;                  // 32-pixel steps per row
+    uint32_t stage_bytes, tx_a, tmem_cols;
+    float *dw;
+    int *err;
+};
+
+// MN-major operand with 64-byte swizzle: atoms of 32 elements x 8 rows,
+// `lbo` bytes apart along M/N, 8-row groups `sbo` bytes apart along K.
+__device__ __forceinline__ uint64_t sdesc_mn64(const void *tile, uint32_t lbo, uint32_t sbo) {
+    const uint64_t a = smem_u32(tile);
+    return ((a >> 4) & 0x3FFFull) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) | (uint64_t((sbo >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// MN-major (bits 15, 16), N/8 in bits 17-22, M/16 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | (uint32_t(n >> 3) << 17) |
+           (uint32_t(m >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 1)
+k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapDY, const WgradArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[WG_STAGES], empty[WG_STAGES], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mtile = blockIdx.x;
+    const long long row0 = (long long)blockIdx.y * a.rows_per_cta;
+    long long row1 = row0 + a.rows_per_cta;
+    if (row1 > (long long)a.n * a.h) row1 = (long long)a.n * a.h;
+    const int iters = row1 > row0 ? int((row1 - row0) * a.xsteps) : 0;
+    const int nb = a.cy / 32;  // dy boxes (N atoms)
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < WG_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, a.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int i = 0; i < iters; ++i) {
+                const int s = i % WG_STAGES, use = i / WG_STAGES;
+                if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 21)) break;
+                const long long row = row0 + i / a.xsteps;
+                const int img = int(row / a.h), y = int(row % a.h);
+                const int x0 = (i % a.xsteps) * WG_KP;
+                uint8_t *st = smem + size_t(s) * a.stage_bytes;
+                int nload = 0;
+                for (int j = 0; j < 4; ++j) nload += (mtile * 4 + j < a.nf) ? 1 : 0;
+                mbar_expect_tx(&full[s], uint32_t(nload + nb) * WG_BOX);
+                for (int j = 0; j < 4; ++j) {
+                    const int f = mtile * 4 + j;
+                    if (f >= a.nf) break;
+                    const int tap = f / a.nchunk, ch = f - tap * a.nchunk;
+                    const int dy = a.k == 3 ? tap / 3 - 1 : 0, dx = a.k == 3 ? tap % 3 - 1 : 0;
+                    tma_load_4d(st + j * WG_BOX, &mapX, &full[s], ch * 32, x0 + dx, y + dy, img);
+                }
+                for (int b = 0; b < nb; ++b) tma_load_4d(st + (4 + b) * WG_BOX, &mapDY, &full[s], b * 32, x0, y, img);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_mn(128, a.cy);
+            bool ok = true;
+            for (int i = 0; i < iters; ++i) {
+                const int s = i % WG_STAGES, use = i / WG_STAGES;
+                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 22)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint8_t *st = smem + size_t(s) * a.stage_bytes;
+#pragma unroll
+                for (int kk = 0; kk < WG_KP / 16; ++kk) {  // K = 16 pixels per MMA: two 8-pixel groups
+                    const uint64_t ad = sdesc_mn64(st + kk * 1024, WG_BOX, 512);
+                    const uint64_t bd = sdesc_mn64(st + 4 * WG_BOX + kk * 1024, WG_BOX, 512);
+                    umma_bf16(tmem, ad, bd, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
+                umma_commit(&empty[s]);
+            }
+            if (ok && iters > 0) umma_commit(&done);
+        }
+    } else if (iters > 0) {
+        const int q = warp & 3;  // TMEM lanes 32q..: box q of this M tile
+        const int f = mtile * 4 + q;
+        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 23);
+        tc_fence_after();
+        const int tap = f / a.nchunk, ch = f - tap * a.nchunk;
+        const int c = ch * 32 + lane;
+        const bool ok = have && f < a.nf && c < a.cin;
+        const int kk2 = a.k * a.k;
+        for (int o = 0; o < a.cy && have; o += 16) {
+            float v[16];
+            tmem_ld16(tmem + uint32_t(o) + (uint32_t(q * 32) << 16), v);
+            if (!ok) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (o + j < a.cout) atomicAdd(&a.dw[((long long)(o + j) * a.cin + c) * kk2 + tap], v[j]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+// Weights of the input-gradient convolution: the forward weights flipped in
+// space and with input and output channels swapped,
+// wt[tap][c (cin_pad)][o (cout_pad)] = W[o][c][k*k - 1 - tap], BF16, zero padded.
+__global__ void k_pack_w_flip(const float *__restrict__ w, int cout, int cin, int k, int cin_pad, int cout_pad,
+                              __nv_bfloat16 *__restrict__ wt) {
+    const long long total = (long long)k * k * cin_pad * cout_pad;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int o = int(i % cout_pad);
+        const int c = int((i / cout_pad) % cin_pad);
+        const int tap = int(i / ((long long)cout_pad * cin_pad));
+        float v = 0.0f;
+        if (o < cout && c < cin) v = w[((long long)o * cin + c) * k * k + (k * k - 1 - tap)];
+        wt[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// db[c] += sum over images and pixels of dy (FP32 NCHW, sample stride dybs):
+// block (c, part) sums a slice of channel c's planes, then one atomic.
+__global__ void k_bias_grad(const float *__restrict__ dy, long long dybs, int n, long long hw, float *__restrict__ db) {
+    const int c = blockIdx.x;
+    const long long total = (long long)n * hw;
+    double s = 0.0;
+    for (long long i = blockIdx.y * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.y * blockDim.x) {
+        const long long img = i / hw, p = i - img * hw;
+        s += dy[img * dybs + (long long)c * hw + p];
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&db[c], float(sh[0]));
+}
+
+// NHWC BF16 activations as an MN-major operand: dims (channels, w, h, n),
+// box (32 channels, 32 pixels, 1, 1), 64-byte swizzle.
+bool map_wgrad(CUtensorMap *m, const void *ptr, int c, int w, int h, int n) {
+    const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
+    const cuuint64_t strides[3] = {cuuint64_t(c) * 2, cuuint64_t(c) * 2 * w, cuuint64_t(c) * 2 * w * h};
+    const cuuint32_t box[4] = {32, WG_KP, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin, const void *dy, int cy, int cout,
+                                             int n, int h, int w, int k, float *dw, int *err, void *stream) {
+    if (!x || !dy || !dw || !err) return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: x, dy, dw and err are required");
+    if (n < 1 || h < 1 || w < 1 || (k != 1 && k != 3))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: need n, h, w >= 1 and k = 1 or 3");
+    if (cx < 32 || cx % 32 || cin < 1 || cin > cx || cy < 32 || cy % 32 || cy > 256 || cout < 1 || cout > cy)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: need cx, cy multiples of 32 (cy <= 256), 1 <= cin <= cx, "
+                                   "1 <= cout <= cy");
+    if ((uintptr_t(x) | uintptr_t(dy)) & 15u) return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: arrays must be 16-byte aligned");
+    if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_wgrad: cuTensorMapEncodeTiled is not available");
+    CUtensorMap mX, mDY;
+    if (!map_wgrad(&mX, x, cx, w, h, n) || !map_wgrad(&mDY, dy, cy, w, h, n))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: tensor map rejected");
+    WgradArgs a;
+    a.n = n;
+    a.h = h;
+    a.w = w;
+    a.k = k;
+    a.nchunk = cx / 32;
+    a.nf = k * k * a.nchunk;
+    a.cin = cin;
+    a.cout = cout;
+    a.cy = cy;
+    a.xsteps = (w + WG_KP - 1) / WG_KP;
+    a.stage_bytes = uint32_t((4 + cy / 32) * WG_BOX);
+    a.tx_a = 4 * WG_BOX;
+    a.tmem_cols = 32;
+    while (a.tmem_cols < uint32_t(cy)) a.tmem_cols <<= 1;
+    a.dw = dw;
+    a.err = err;
+    const int mtiles = (a.nf + 3) / 4;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv_wgrad: device query");
+    // split the n*h rows so that about 2 CTAs per SM run, each >= 4 rows
+    const long long rows = (long long)n * h;
+    long long splits = (2LL * nsm + mtiles - 1) / mtiles;
+    if (splits > rows / 4) splits = rows / 4;
+    if (splits < 1) splits = 1;
+    if (splits > 65535) splits = 65535;
+    a.rows_per_cta = int((rows + splits - 1) / splits);
+    splits = (rows + a.rows_per_cta - 1) / a.rows_per_cta;
+    const size_t smem = 1024 + size_t(WG_STAGES) * a.stage_bytes;
+    e = cudaFuncSetAttribute(k_tc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv_wgrad: shared memory attribute");
+    k_tc_wgrad<<<dim3(unsigned(mtiles), unsigned(splits)), WG_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(
+        mX, mDY, a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv_wgrad launch");
+}
+
+extern "C" glbm_status glbm_nn_tc_pack_weights_flip(const float *wf, int cout, int cin, int k, int cin_pad,
+                                                    int cout_pad, void *wt, void *stream) {
+    if (!wf || !wt || cout < 1 || cin < 1 || (k != 1 && k != 3) || cin_pad < cin || cout_pad < cout)
+        return tcfail(GLBM_EINVAL, "nn_tc_pack_weights_flip: invalid sizes or pointers");
+    const long long total = (long long)k * k * cin_pad * cout_pad;
+    k_pack_w_flip<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        wf, cout, cin, k, cin_pad, cout_pad, static_cast<__nv_bfloat16 *>(wt));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_pack_weights_flip launch");
+}
+
+extern "C" glbm_status glbm_nn_bias_grad(const float *dy, long long dybs, int c, int n, int h, int w, float *db,
+                                         void *stream) {
+    if (!dy || !db || c < 1 || n < 1 || h < 1 || w < 1 || dybs < (long long)c * h * w)
+        return tcfail(GLBM_EINVAL, "nn_bias_grad: invalid sizes or pointers");
+    const long long hw = (long long)h * w;
+    long long parts = ((long long)n * hw + 256 * 64 - 1) / (256 * 64);
+    if (parts > 1024) parts = 1024;
+    k_bias_grad<<<dim3(unsigned(c), unsigned(parts)), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, dybs, n, hw, db);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_bias_grad launch");
+}

@@ -83,6 +83,10 @@ class UNet:
         self._version = 0     # bumped whenever the parameters change
         self._tc = None       # (version, packed BF16 weights, padded biases)
         self._tc_bufs = {}
+        self._train_tc = False  # forward/backward on the tensor cores (set per call)
+        self._tct = None      # (version, flipped BF16 weights) for input gradients
+        self._xh = {}         # BF16 NHWC copy of each convolution's input (training)
+        self._gh = {}         # BF16 NHWC output gradients (training scratch)
 
     # -- plumbing -----------------------------------------------------------
     def _stream(self):
@@ -90,19 +94,23 @@ class UNet:
 
     def _ok(self, rc, what):
         if rc != 0:
-            raise GLBMError(rc, f"{what} failed")
+            raise GLBMError(rc, f"{what} failed: {self.lib.glbm_last_error(None).decode()}")
 
     def _wb(self, name):
         ow, ob = self.offsets[name]
         return ow, ob
 
     def _conv(self, x, xbs, cin, y, ybs, cout, n, h, w, k, name, relu, xoff=0, yoff=0):
+        if self._train_tc:
+            return self._conv_tc(x, cin, y, cout, n, h, w, k, name, relu)
         ow, ob = self._wb(name)
         self._ok(self.lib.glbm_nn_conv_fwd(_ptr(x, xoff), xbs, cin, _ptr(y, yoff), ybs, cout, n, h, w, k,
                                            _ptr(self.params, ow), _ptr(self.params, ob), int(relu),
                                            self._stream()), "conv_fwd")
 
     def _conv_bwd(self, x, xbs, cin, dy, dybs, cout, n, h, w, k, name, dx=None, dxbs=0):
+        if self._train_tc:
+            return self._conv_bwd_tc(cin, dy, cout, n, h, w, k, name, dx)
         ow, ob = self._wb(name)
         self._ok(self.lib.glbm_nn_conv_bwd_weight(_ptr(x), xbs, cin, _ptr(dy), dybs, cout, n, h, w, k,
                                                   _ptr(self.grads, ow), _ptr(self.grads, ob),
@@ -145,8 +153,14 @@ class UNet:
         return B
 
     # -- network ------------------------------------------------------------
-    def forward(self, x):
-        """x: contiguous (n, in_ch, h, w) float32 CUDA tensor -> (n, out_ch, h, w)."""
+    def forward(self, x, tc=False):
+        """x: contiguous (n, in_ch, h, w) float32 CUDA tensor -> (n, out_ch, h, w).
+        tc: run the convolutions on the tensor cores (BF16 operands, FP32
+        accumulation and FP32 NCHW activations between layers), keeping what
+        backward(tc=True) needs."""
+        self._train_tc = bool(tc)
+        if tc:
+            self._tc_pack()
         n, _, h, w = x.shape
         B = self._buffers(n, h, w)
         self._x = x
@@ -173,11 +187,19 @@ class UNet:
             self._conv(B[f"da{l}"], c * hl * wl, c, B[f"d{l}"], c * hl * wl, c, n, hl, wl, 3, f"d{l}b", True)
             top, ctop = B[f"d{l}"], c
         self._conv(top, ctop * h * w, ctop, B["y"], self.out_ch * h * w, self.out_ch, n, h, w, 1, "head", False)
+        self._train_tc = False
         return B["y"]
 
-    def backward(self, gy):
+    def backward(self, gy, tc=False):
         """Gradients of the loss w.r.t. the parameters (into self.grads) given
-        gy = dL/dy of the last forward call."""
+        gy = dL/dy of the last forward call (tc: on the tensor cores; the
+        forward call must have used tc=True too)."""
+        if tc and not self._xh:
+            raise RuntimeError("backward(tc=True) needs a forward(tc=True) first")
+        self._train_tc = bool(tc)
+        if tc:
+            self._tc_pack()
+            self._tc_pack_flip()
         x = self._x
         n, _, h, w = x.shape
         B = self._buffers(n, h, w)
@@ -219,6 +241,74 @@ class UNet:
                 cp = self.ch[l - 1]
                 self._conv_bwd(B[f"p{l - 1}"], cp * hl * wl, cp, B[f"ga{l}"], c * hl * wl, c, n, hl, wl, 3,
                                f"e{l}a", dx=B[f"gp{l - 1}"], dxbs=cp * hl * wl)
+        self._train_tc = False
+
+    # -- tensor-core training ------------------------------------------------
+    def _nhwc(self, store, key, src, c, n, h, w):
+        """FP32 NCHW src (c channels) -> BF16 NHWC with max(32, c rounded up to
+        32) channels, zero padded; kept in store[key]."""
+        torch = self.torch
+        cp = max(32, self._pad(c, 32))
+        buf = store.get(key)
+        if buf is None or tuple(buf.shape) != (n, h, w, cp):
+            buf = torch.empty((n, h, w, cp), dtype=torch.bfloat16, device="cuda")
+            store[key] = buf
+        self._ok(self.lib.glbm_nn_nchw_to_nhwc(_ptr(src), n, c, h, w, C.c_void_p(buf.data_ptr()), cp,
+                                               self._stream()), "nchw_to_nhwc")
+        return buf, cp
+
+    def _tc_err(self):
+        torch = self.torch
+        if getattr(self, "_tc_errbuf", None) is None:
+            self._tc_errbuf = torch.zeros(1, dtype=torch.int32, device="cuda")
+        return C.c_void_p(self._tc_errbuf.data_ptr())
+
+    def _conv_tc(self, x, cin, y, cout, n, h, w, k, name, relu):
+        xh, cp = self._nhwc(self._xh, name, x, cin, n, h, w)
+        _, W, Bs = self._tc
+        cop = Bs[name].numel()
+        self._ok(self.lib.glbm_nn_tc_conv(
+            C.c_void_p(xh.data_ptr()), cp, None, 0, n, h, w, k, C.c_void_p(W[name].data_ptr()),
+            C.c_void_p(Bs[name].data_ptr()), cop, _ptr(y), cop, int(relu), 1, cout, self._tc_err(),
+            self._stream()), "tc_conv")
+
+    def _conv_bwd_tc(self, cin, dy, cout, n, h, w, k, name, dx):
+        xh = self._xh[name]
+        dyh, cyp = self._nhwc(self._gh, (n, h, w, cout), dy, cout, n, h, w)
+        ow, ob = self._wb(name)
+        self._ok(self.lib.glbm_nn_tc_conv_wgrad(C.c_void_p(xh.data_ptr()), xh.shape[3], cin,
+                                                C.c_void_p(dyh.data_ptr()), cyp, cout, n, h, w, k,
+                                                _ptr(self.grads, ow), self._tc_err(), self._stream()), "tc_wgrad")
+        self._ok(self.lib.glbm_nn_bias_grad(_ptr(dy), cout * h * w, cout, n, h, w, _ptr(self.grads, ob),
+                                            self._stream()), "bias_grad")
+        if dx is not None:
+            _, WF, ZB = self._tct
+            cip = WF[name].numel() // (k * k * cyp)
+            self._ok(self.lib.glbm_nn_tc_conv(
+                C.c_void_p(dyh.data_ptr()), cyp, None, 0, n, h, w, k, C.c_void_p(WF[name].data_ptr()),
+                C.c_void_p(ZB[cip].data_ptr()), cip, _ptr(dx), cip, 0, 1, cin, self._tc_err(),
+                self._stream()), "tc_conv (input gradient)")
+
+    def _tc_pack_flip(self):
+        """BF16 weights of the input-gradient convolutions (flipped in space,
+        input and output channels swapped), repacked when the parameters
+        change."""
+        if self._tct is not None and self._tct[0] == self._version:
+            return self._tct
+        torch = self.torch
+        WF, ZB = {}, {}
+        for name, ci, co, k in self.specs:
+            cyp = max(32, self._pad(co, 32))      # input channels of the gradient convolution
+            cip = max(16, self._pad(ci, 16))      # its output channels
+            wt = torch.empty(k * k * cip * cyp, dtype=torch.bfloat16, device="cuda")
+            ow, _ = self._wb(name)
+            self._ok(self.lib.glbm_nn_tc_pack_weights_flip(_ptr(self.params, ow), co, ci, k, cip, cyp,
+                                                           C.c_void_p(wt.data_ptr()), self._stream()), "pack_flip")
+            WF[name] = wt
+            if cip not in ZB:
+                ZB[cip] = torch.zeros(cip, dtype=torch.float32, device="cuda")
+        self._tct = (self._version, WF, ZB)
+        return self._tct
 
     def loss(self, pred, target, channel_weight, with_grad=True):
         torch = self.torch
@@ -384,9 +474,12 @@ class UNet:
 
     def tc_error(self):
         """Nonzero if a tensor-core pipeline wait timed out since the buffers
-        were made (synchronises)."""
+        were made, in inference or training (synchronises)."""
         for B in self._tc_bufs.values():
-            return int(B["err"].item())
+            if int(B["err"].item()):
+                return int(B["err"].item())
+        if getattr(self, "_tc_errbuf", None) is not None:
+            return int(self._tc_errbuf.item())
         return 0
 
 

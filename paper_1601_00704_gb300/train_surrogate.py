@@ -89,9 +89,12 @@ def augment(x, y, rng):
     return np.ascontiguousarray(x), np.ascontiguousarray(y)
 
 
-def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0)):
+def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0), tc=False):
     """X, Y: one (count, 3, n, n) array pair, or lists of pairs of different
-    sizes (each batch is drawn from one size; sizes interleave)."""
+    sizes (each batch is drawn from one size; sizes interleave).  tc: every
+    convolution (forward, input gradient, weight gradient) on the tensor
+    cores with BF16 operands and FP32 accumulation; FP32 master weights and
+    Adam either way."""
     if not isinstance(X, (list, tuple)):
         X, Y = [X], [Y]
     import torch
@@ -113,11 +116,11 @@ def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0)):
             ty = torch.from_numpy(yb).cuda()
             # cosine learning-rate decay
             lr_t = 0.5 * lr * (1 + np.cos(np.pi * it / total))
-            pred = net.forward(tx)
+            pred = net.forward(tx, tc=tc)
             loss, g = net.loss(pred, ty, CHANNEL_WEIGHT)
             if coarse:
                 loss = loss + net.coarse_loss(pred, ty, coarse[0], coarse[1], g)
-            net.backward(g)
+            net.backward(g, tc=tc)
             net.adam_step(lr_t)
             acc += float(loss.item()) * len(idx)
             cnt += len(idx)
@@ -125,6 +128,43 @@ def train(net, X, Y, epochs, batch, lr, seed=0, log=print, coarse=(8, 4.0)):
         hist.append(acc / cnt)
         log(f"epoch {ep + 1}/{epochs}: loss {hist[-1]:.5f} ({time.perf_counter() - t0:.0f} s)")
     return hist
+
+
+def time_training(batches, batch, n, base, levels, max_ch, seed=0):
+    """CUDA-event seconds of `batches` training steps (forward, loss,
+    backward, Adam) on random n x n data, FP32 kernels vs tensor cores, after
+    two warm-up steps each."""
+    import torch
+
+    from paper_1601_00704_gb300 import surrogate
+    rng = np.random.default_rng(seed)
+    x = torch.from_numpy(rng.normal(size=(batch, 3, n, n)).astype(np.float32)).cuda()
+    y = torch.from_numpy(rng.normal(size=(batch, 3, n, n)).astype(np.float32)).cuda()
+    out = {"batches": batches, "batch": batch, "n": n, "levels": levels, "base": base, "max_ch": max_ch}
+    for tc in (False, True):
+        net = surrogate.UNet(base=base, levels=levels, seed=seed, max_ch=max_ch)
+
+        def step():
+            pred = net.forward(x, tc=tc)
+            _, g = net.loss(pred, y, CHANNEL_WEIGHT)
+            net.backward(g, tc=tc)
+            net.adam_step(1e-4)
+        step()
+        step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(batches):
+            step()
+        e1.record()
+        e1.synchronize()
+        if tc and net.tc_error():
+            raise RuntimeError("tensor-core pipeline reported a timeout")
+        out["tc" if tc else "fp32"] = {"seconds": e0.elapsed_time(e1) * 1e-3,
+                                       "ms_per_step": e0.elapsed_time(e1) / batches}
+    out["speedup"] = out["fp32"]["seconds"] / out["tc"]["seconds"]
+    return out
 
 
 def predict(net, eps, K, tc=False):
@@ -163,6 +203,11 @@ def main(argv=None):
                         "medium of the training recipe, then exit")
     p.add_argument("--weights", default=DEFAULT_WEIGHTS, help="weights for --infer")
     p.add_argument("--fp32", action="store_true", help="--infer with the FP32 kernels instead of the tensor cores")
+    p.add_argument("--tc", action="store_true",
+                   help="train on the tensor cores (BF16 operands, FP32 accumulation and master weights)")
+    p.add_argument("--time-epoch", type=int, metavar="BATCHES",
+                   help="time BATCHES training steps (batch --batch, --n^2 random data) with the FP32 kernels "
+                        "and with the tensor cores, then exit")
     a = p.parse_args(argv)
     from paper_1601_00704_gb300 import build
     build.build()
@@ -171,6 +216,9 @@ def main(argv=None):
         net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)
         net.load(a.weights)
         print(json.dumps(infer_timing(net, a.infer, tc=not a.fp32)))
+        return
+    if a.time_epoch:
+        print(json.dumps(time_training(a.time_epoch, a.batch, a.n, a.base, a.levels, a.max_ch)))
         return
     if a.study_only:
         net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)
@@ -184,10 +232,11 @@ def main(argv=None):
     net = surrogate.UNet(base=a.base, levels=a.levels, seed=a.seed, max_ch=a.max_ch)
     t0 = time.perf_counter()
     hist = train(net, X, Y, a.epochs, a.batch, a.lr, seed=a.seed,
-                 coarse=(8, a.coarse) if a.coarse > 0 else None)
+                 coarse=(8, a.coarse) if a.coarse > 0 else None, tc=a.tc)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     net.save(a.out, half=True)
     rec = {"dataset": info, "epochs": a.epochs, "batch": a.batch, "lr": a.lr, "base": a.base,
+           "kernels": "tensor cores (BF16 operands, FP32 accumulation)" if a.tc else "FP32",
            "levels": a.levels, "max_ch": a.max_ch, "coarse_weight": a.coarse, "channel_weight": CHANNEL_WEIGHT, "loss": hist,
            "train_seconds": time.perf_counter() - t0, "params": int(net.nparams)}
     with open(os.path.splitext(a.out)[0] + ".json", "w") as fh:

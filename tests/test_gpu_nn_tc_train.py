@@ -1,0 +1,139 @@
+"""Tensor-core training kernels of the warm-start network against the FP64
+NumPy oracle: the weight gradient (tcgen05, MN-major operands from BF16 NHWC
+activations) on the same BF16-rounded inputs, the bias gradient, the flipped
+weight packing of the input gradient, and whole-network gradients of the
+tensor-core backward pass."""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import unet as ou
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_1601_00704_gb300 import build
+    build.build()
+    import paper_1601_00704_gb300 as p
+    p.load()
+    return p
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _vp(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _st():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _nhwc(a, cpad):
+    """(n, c, h, w) float64 -> BF16 NHWC device tensor with cpad channels."""
+    import torch
+    n, c, h, w = a.shape
+    out = np.zeros((n, h, w, cpad), dtype=np.float32)
+    out[..., :c] = a.transpose(0, 2, 3, 1)
+    return torch.from_numpy(out).to(torch.bfloat16).cuda()
+
+
+# (n, h, w, cin, cout, k)
+WG_CASES = [
+    (2, 20, 40, 32, 32, 3),    # shallow layer, ragged 32-pixel steps
+    (1, 16, 70, 3, 32, 3),     # first layer: 3 real input channels padded to 32
+    (2, 9, 33, 96, 64, 3),     # concatenated decoder input, 27 (tap, chunk) boxes: a partial M tile
+    (1, 8, 64, 128, 128, 3),   # wide layer, 4 output boxes
+    (2, 12, 40, 32, 3, 1),     # 1x1 head, 3 real output channels padded to 32
+    (1, 4, 16, 256, 256, 3),   # the widest channel counts, image narrower than a step
+]
+
+
+@pytest.mark.parametrize("n,h,w,cin,cout,k", WG_CASES)
+def test_wgrad_matches_oracle(pkg, n, h, w, cin, cout, k):
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(hash((n, h, w, cin, cout, k)) % 2 ** 32)
+    x = _bf16(rng.normal(size=(n, cin, h, w)))
+    dy = _bf16(rng.normal(size=(n, cout, h, w)))
+    W = np.zeros((cout, cin, k, k))
+    _, dW, db = ou.conv_backward(x, W, dy)
+    cx, cy = max(32, -(-cin // 32) * 32), max(32, -(-cout // 32) * 32)
+    xd, dyd = _nhwc(x, cx), _nhwc(dy, cy)
+    dw = torch.full((cout * cin * k * k,), 0.25, dtype=torch.float32, device="cuda")  # accumulates
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.glbm_nn_tc_conv_wgrad(_vp(xd), cx, cin, _vp(dyd), cy, cout, n, h, w, k, _vp(dw), _vp(err), _st())
+    assert rc == 0, lib.glbm_last_error(None)
+    dyf = torch.from_numpy(dy.astype(np.float32)).cuda()
+    dbd = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    assert lib.glbm_nn_bias_grad(_vp(dyf), cout * h * w, cout, n, h, w, _vp(dbd), _st()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = dw.cpu().numpy().astype(np.float64).reshape(cout, cin, k, k) - 0.25
+    # FP32 sums of exact BF16 products over n*h*w pixels
+    mag = ou.conv_backward(np.abs(x), W, np.abs(dy))[1]
+    np.testing.assert_allclose(got, dW, rtol=0, atol=1e-5 * mag.max() + 1e-6)
+    np.testing.assert_allclose(dbd.cpu().numpy(), db, rtol=1e-5, atol=1e-4)
+
+
+def test_pack_weights_flip(pkg):
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(7)
+    cout, cin, k, cip, cop = 24, 40, 3, 48, 32
+    wf = rng.normal(size=(cout, cin, k, k)).astype(np.float32)
+    wt = torch.empty(k * k * cip * cop, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_pack_weights_flip(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, cin, k, cip, cop,
+                                            _vp(wt), _st()) == 0
+    got = wt.float().cpu().numpy().reshape(k * k, cip, cop)
+    exp = np.zeros((k * k, cip, cop), dtype=np.float32)
+    flipped = wf[:, :, ::-1, ::-1].reshape(cout, cin, k * k)  # [o][c][tap'] with tap' = 8 - tap
+    exp[:, :cin, :cout] = flipped.transpose(2, 1, 0)
+    assert np.array_equal(got, torch.from_numpy(exp).to(torch.bfloat16).float().numpy())
+
+
+@pytest.mark.parametrize("levels,max_ch,size,batch", [(3, 64, 32, 2), (4, None, 64, 2)])
+def test_unet_tc_gradients_match_oracle(pkg, levels, max_ch, size, batch):
+    """Whole-network gradients of the tensor-core forward and backward passes
+    (BF16 operands at every convolution, FP32 accumulation, FP32 master
+    weights) against the FP64 oracle on the FP32 parameters: per parameter
+    tensor, relative L2 error below 3e-2 -- the BF16 rounding (2^-9
+    relative) of activations and output gradients, accumulated over the
+    layers."""
+    import torch
+    from paper_1601_00704_gb300.surrogate import UNet
+    net = UNet(base=32, levels=levels, seed=5, max_ch=max_ch)
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=(batch, 3, size, size)).astype(np.float32)
+    t = rng.normal(size=(batch, 3, size, size)).astype(np.float32)
+    cw = (1.0, 0.1, 0.1)
+    tx, tt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    pred = net.forward(tx, tc=True)
+    _, g = net.loss(pred, tt, cw)
+    net.backward(g, tc=True)
+    torch.cuda.synchronize()
+    assert net.tc_error() == 0
+    got = net.grads.cpu().numpy().astype(np.float64)
+    specs = list(net.specs)
+    flat = net.params.cpu().numpy().astype(np.float64)
+    params = ou.unpack(flat, specs)
+    y, cache = ou.forward(params, x.astype(np.float64), levels)
+    _, gy = ou.mse(y, t.astype(np.float64), cw)
+    grads, _ = ou.backward(params, cache, gy, levels)
+    ref = ou.pack(grads, specs)
+    off = 0
+    for name, ci, co, k in specs:
+        nw = co * ci * k * k + co
+        a, b = got[off:off + nw], ref[off:off + nw]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print(f"{name}: relative L2 {rel:.2e}")
+        assert rel < 3e-2, (name, rel)
+        off += nw
