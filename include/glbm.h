@@ -517,12 +517,14 @@ glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin,
                                   void *stream);
 
 /* Weights of the input-gradient convolution (dx = conv(dy, these)) from FP32
- * forward weights w [cout][cin][k][k]: BF16 [k^2][cin_pad][cout_pad] with
- * wt[tap][c][o] = w[o][c][k^2 - 1 - tap] (flipped in space, channels
- * swapped), zero padded. */
+ * forward weights w [cout][cin][k][k], for the input channels c_begin ..
+ * c_begin + c_pad - 1 (the gradient convolution's outputs; at most 256 per
+ * call): BF16 [k^2][c_pad][cout_pad] with wt[tap][cc][o] =
+ * w[o][c_begin + cc][k^2 - 1 - tap] (flipped in space, channels swapped),
+ * zero where c_begin + cc >= cin or o >= cout. */
 glbm_status glbm_nn_tc_pack_weights_flip(const float *w, int cout, int cin,
-                                         int k, int cin_pad, int cout_pad,
-                                         void *wt, void *stream);
+                                         int k, int c_begin, int c_pad,
+                                         int cout_pad, void *wt, void *stream);
 
 /* Bias gradient db[c] += sum over images and pixels of dy, FP32 NCHW dy with
  * per-sample stride dybs. */

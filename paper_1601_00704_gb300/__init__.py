@@ -94,7 +94,7 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_batch_set_convergence": ([h, i], i),
         "glbm_nn_tc_set_variant": ([i], None),
         "glbm_nn_tc_conv_wgrad": ([_VP, i, i, _VP, i, i, i, i, i, i, _VP, _VP, _VP], i),
-        "glbm_nn_tc_pack_weights_flip": ([_VP, i, i, i, i, i, _VP, _VP], i),
+        "glbm_nn_tc_pack_weights_flip": ([_VP, i, i, i, i, i, i, _VP, _VP], i),
         "glbm_nn_bias_grad": ([_VP, ll, i, i, i, i, _VP, _VP], i),
         "glbm_batch_get_persistent": ([h, C.POINTER(i)], i),
         "glbm_load": ([h, C.c_char_p], i),

@@ -160,14 +160,14 @@ k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
 // Weights of the input-gradient convolution: the forward weights flipped in
 // space and with input and output channels swapped,
 // wt[tap][c (cin_pad)][o (cout_pad)] = W[o][c][k*k - 1 - tap], BF16, zero padded.
-__global__ void k_pack_w_flip(const float *__restrict__ w, int cout, int cin, int k, int cin_pad, int cout_pad,
-                              __nv_bfloat16 *__restrict__ wt) {
-    const long long total = (long long)k * k * cin_pad * cout_pad;
+__global__ void k_pack_w_flip(const float *__restrict__ w, int cout, int cin, int k, int c_begin, int c_pad,
+                              int cout_pad, __nv_bfloat16 *__restrict__ wt) {
+    const long long total = (long long)k * k * c_pad * cout_pad;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int o = int(i % cout_pad);
-        const int c = int((i / cout_pad) % cin_pad);
-        const int tap = int(i / ((long long)cout_pad * cin_pad));
+        const int c = c_begin + int((i / cout_pad) % c_pad);
+        const int tap = int(i / ((long long)cout_pad * c_pad));
         float v = 0.0f;
         if (o < cout && c < cin) v = w[((long long)o * cin + c) * k * k + (k * k - 1 - tap)];
         wt[i] = __float2bfloat16_rn(v);
@@ -261,13 +261,14 @@ extern "C" glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin, con
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv_wgrad launch");
 }
 
-extern "C" glbm_status glbm_nn_tc_pack_weights_flip(const float *wf, int cout, int cin, int k, int cin_pad,
-                                                    int cout_pad, void *wt, void *stream) {
-    if (!wf || !wt || cout < 1 || cin < 1 || (k != 1 && k != 3) || cin_pad < cin || cout_pad < cout)
+extern "C" glbm_status glbm_nn_tc_pack_weights_flip(const float *wf, int cout, int cin, int k, int c_begin,
+                                                    int c_pad, int cout_pad, void *wt, void *stream) {
+    if (!wf || !wt || cout < 1 || cin < 1 || (k != 1 && k != 3) || c_begin < 0 || c_begin >= cin || c_pad < 1 ||
+        cout_pad < cout)
         return tcfail(GLBM_EINVAL, "nn_tc_pack_weights_flip: invalid sizes or pointers");
-    const long long total = (long long)k * k * cin_pad * cout_pad;
+    const long long total = (long long)k * k * c_pad * cout_pad;
     k_pack_w_flip<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        wf, cout, cin, k, cin_pad, cout_pad, static_cast<__nv_bfloat16 *>(wt));
+        wf, cout, cin, k, c_begin, c_pad, cout_pad, static_cast<__nv_bfloat16 *>(wt));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_pack_weights_flip launch");
 }

@@ -282,12 +282,26 @@ class UNet:
         self._ok(self.lib.glbm_nn_bias_grad(_ptr(dy), cout * h * w, cout, n, h, w, _ptr(self.grads, ob),
                                             self._stream()), "bias_grad")
         if dx is not None:
+            # the gradient convolution has cin outputs, run in groups of at
+            # most 256 (the MMA's N); a group beyond the first writes a
+            # scratch tensor that is copied into its channel slice of dx
             _, WF, ZB = self._tct
-            cip = WF[name].numel() // (k * k * cyp)
-            self._ok(self.lib.glbm_nn_tc_conv(
-                C.c_void_p(dyh.data_ptr()), cyp, None, 0, n, h, w, k, C.c_void_p(WF[name].data_ptr()),
-                C.c_void_p(ZB[cip].data_ptr()), cip, _ptr(dx), cip, 0, 1, cin, self._tc_err(),
-                self._stream()), "tc_conv (input gradient)")
+            for c0, cg, cgp, wt in WF[name]:
+                out = dx if len(WF[name]) == 1 else self._dx_scratch(n, cg, h, w)
+                self._ok(self.lib.glbm_nn_tc_conv(
+                    C.c_void_p(dyh.data_ptr()), cyp, None, 0, n, h, w, k, C.c_void_p(wt.data_ptr()),
+                    C.c_void_p(ZB[cgp].data_ptr()), cgp, _ptr(out), cgp, 0, 1, cg, self._tc_err(),
+                    self._stream()), "tc_conv (input gradient)")
+                if out is not dx:
+                    self._ok(self.lib.glbm_nn_copy_channels(_ptr(out), cg * h * w, _ptr(dx, c0 * h * w), cin * h * w,
+                                                            cg, n, h, w, 0, self._stream()), "copy")
+
+    def _dx_scratch(self, n, c, h, w):
+        torch = self.torch
+        t = getattr(self, "_dxs", None)
+        if t is None or t.numel() < n * c * h * w:
+            t = self._dxs = torch.empty(n * c * h * w, dtype=torch.float32, device="cuda")
+        return t
 
     def _tc_pack_flip(self):
         """BF16 weights of the input-gradient convolutions (flipped in space,
@@ -299,14 +313,18 @@ class UNet:
         WF, ZB = {}, {}
         for name, ci, co, k in self.specs:
             cyp = max(32, self._pad(co, 32))      # input channels of the gradient convolution
-            cip = max(16, self._pad(ci, 16))      # its output channels
-            wt = torch.empty(k * k * cip * cyp, dtype=torch.bfloat16, device="cuda")
-            ow, _ = self._wb(name)
-            self._ok(self.lib.glbm_nn_tc_pack_weights_flip(_ptr(self.params, ow), co, ci, k, cip, cyp,
-                                                           C.c_void_p(wt.data_ptr()), self._stream()), "pack_flip")
-            WF[name] = wt
-            if cip not in ZB:
-                ZB[cip] = torch.zeros(cip, dtype=torch.float32, device="cuda")
+            WF[name] = []
+            for c0 in range(0, ci, 256):           # its outputs, in groups of <= 256
+                cg = min(256, ci - c0)
+                cgp = max(16, self._pad(cg, 16))
+                wt = torch.empty(k * k * cgp * cyp, dtype=torch.bfloat16, device="cuda")
+                ow, _ = self._wb(name)
+                self._ok(self.lib.glbm_nn_tc_pack_weights_flip(_ptr(self.params, ow), co, ci, k, c0, cgp, cyp,
+                                                               C.c_void_p(wt.data_ptr()), self._stream()),
+                         "pack_flip")
+                WF[name].append((c0, cg, cgp, wt))
+                if cgp not in ZB:
+                    ZB[cgp] = torch.zeros(cgp, dtype=torch.float32, device="cuda")
         self._tct = (self._version, WF, ZB)
         return self._tct
 

@@ -88,16 +88,18 @@ def test_pack_weights_flip(pkg):
     import torch
     lib = pkg.load()
     rng = np.random.default_rng(7)
-    cout, cin, k, cip, cop = 24, 40, 3, 48, 32
+    cout, cin, k, cop = 24, 40, 3, 32
     wf = rng.normal(size=(cout, cin, k, k)).astype(np.float32)
-    wt = torch.empty(k * k * cip * cop, dtype=torch.bfloat16, device="cuda")
-    assert lib.glbm_nn_tc_pack_weights_flip(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, cin, k, cip, cop,
-                                            _vp(wt), _st()) == 0
-    got = wt.float().cpu().numpy().reshape(k * k, cip, cop)
-    exp = np.zeros((k * k, cip, cop), dtype=np.float32)
     flipped = wf[:, :, ::-1, ::-1].reshape(cout, cin, k * k)  # [o][c][tap'] with tap' = 8 - tap
-    exp[:, :cin, :cout] = flipped.transpose(2, 1, 0)
-    assert np.array_equal(got, torch.from_numpy(exp).to(torch.bfloat16).float().numpy())
+    wd = torch.from_numpy(wf.ravel()).cuda()
+    for c_begin, cpad in ((0, 48), (16, 32)):  # all input channels, and a group of them
+        wt = torch.empty(k * k * cpad * cop, dtype=torch.bfloat16, device="cuda")
+        assert lib.glbm_nn_tc_pack_weights_flip(_vp(wd), cout, cin, k, c_begin, cpad, cop, _vp(wt), _st()) == 0
+        got = wt.float().cpu().numpy().reshape(k * k, cpad, cop)
+        exp = np.zeros((k * k, cpad, cop), dtype=np.float32)
+        nc = min(cpad, cin - c_begin)
+        exp[:, :nc, :cout] = flipped[:, c_begin:c_begin + nc].transpose(2, 1, 0)
+        assert np.array_equal(got, torch.from_numpy(exp).to(torch.bfloat16).float().numpy())
 
 
 @pytest.mark.parametrize("levels,max_ch,size,batch", [(3, 64, 32, 2), (4, None, 64, 2)])
