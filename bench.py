@@ -372,7 +372,7 @@ RHO_CH4 = 0.717         # kg/m^3, methane at standard conditions
 MDARCY = 9.869233e-16   # m^2
 
 
-BATCH_TOL, BATCH_CHECK, BATCH_PATIENCE, BATCH_MAX = 3e-6, 1000, 3, 300_000
+BATCH_TOL, BATCH_CHECK, BATCH_PATIENCE, BATCH_MAX = 1e-5, 1000, 3, 300_000
 
 
 def batch_bench(a):
