@@ -217,13 +217,16 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     const int ntile_w = 9 * a.nchunk;
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(ntile_w) * a.wtile;
+    uint8_t *sO = sA + size_t(a.stages) * a.stage_bytes;  // epilogue staging, 4 warps x 32 pixels x cout
     constexpr int SMAX = 3;
     __shared__ __align__(8) uint64_t full[SMAX], empty[SMAX], wfull, accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    __shared__ float sbias[64];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = a.stages;
+    if (threadIdx.x < a.cout) sbias[threadIdx.x] = a.bias[threadIdx.x];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -318,7 +321,13 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             }
         }
     } else {
+        // Epilogue: per output row, each lane converts its pixel's cout
+        // channels and parks them in this warp's staging slot (32 pixels x
+        // cout BF16); the warp then writes the 32 pixels with 16-byte stores
+        // that are contiguous across lanes.
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
+        const int c8 = a.cout / 8;  // 16-byte chunks per pixel
+        uint4 *so = reinterpret_cast<uint4 *>(sO + size_t(q) * 32 * a.cout * 2);
         long long t = 0;
         for (long long band = blockIdx.x; band < a.nbands; band += gridDim.x, ++t) {
             const int ab = int(t & 1);
@@ -327,21 +336,18 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             const int bx = int(band % a.nbx);
             const long long rest = band / a.nbx;
             const int by = int(rest % a.nby), img = int(rest / a.nby);
-            const int px = bx * TC_M + q * 32 + lane;
+            const int px0 = bx * TC_M + q * 32;  // this warp's first pixel
             for (int r = 0; r < a.R; ++r) {
                 const int py = by * a.R + r;
-                const bool ok = px < a.w && py < a.h;
-                const long long pixel = ((long long)img * a.h + py) * a.w + px;
                 for (int c = 0; c < a.cout; c += 16) {
                     float v[16];
                     tmem_ld16(tmem + uint32_t(ab) * a.acc_cols + uint32_t(r) * a.acc_row + uint32_t(c) +
                                   (uint32_t(q * 32) << 16),
                               v);
-                    if (!ok) continue;
                     uint32_t pk[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        float lo = v[2 * j] + a.bias[c + 2 * j], hi = v[2 * j + 1] + a.bias[c + 2 * j + 1];
+                        float lo = v[2 * j] + sbias[c + 2 * j], hi = v[2 * j + 1] + sbias[c + 2 * j + 1];
                         if (a.relu) {
                             lo = fmaxf(lo, 0.0f);
                             hi = fmaxf(hi, 0.0f);
@@ -349,10 +355,19 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                         __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
                         pk[j] = *reinterpret_cast<uint32_t *>(&b2);
                     }
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) + pixel * a.ys + c);
-                    dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    so[lane * c8 + c / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    so[lane * c8 + c / 8 + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
+                __syncwarp();
+                if (py < a.h) {
+                    __nv_bfloat16 *yrow = static_cast<__nv_bfloat16 *>(a.y) + (((long long)img * a.h + py) * a.w) * a.ys;
+                    for (int u = lane; u < 32 * c8; u += 32) {
+                        const int p = u / c8, ch = u - p * c8;
+                        if (px0 + p < a.w)
+                            *reinterpret_cast<uint4 *>(yrow + (long long)(px0 + p) * a.ys + ch * 8) = so[u];
+                    }
+                }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -519,8 +534,9 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
     for (; r >= 1; --r) {
         const size_t blk = (size_t(r + 2) * BAND_PX * 16 + 127) / 128 * 128;
         const size_t stage = 4 * blk;
+        const size_t staging = size_t(4) * 32 * cout * 2;
         for (int st = 3; st >= 2; --st) {
-            const size_t total = 1024 + wbytes + st * stage;
+            const size_t total = 1024 + wbytes + st * stage + staging;
             if (total <= kSmemLimit) {
                 *R = r;
                 *stages = st;
