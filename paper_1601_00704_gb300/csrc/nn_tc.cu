@@ -179,10 +179,16 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 // ((r+1+dy) * 130 + 1+dx) * 16 bytes in: core matrices of 8 pixels are 128 B
 // apart along M (SBO) and 8-channel blocks one block stride apart along K
 // (LBO).  Each band accumulates R rows into one of two TMEM buffers, so the
-// epilogue of one band overlaps the MMAs of the next.  Roles as in the tile
-// kernel: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue; every wait bounded.
+// epilogue of one band overlaps the MMAs of the next.  The halo is copied by
+// three producer warps with 16-byte cp.async (zero-filled outside the
+// image): a TMA box with 16-byte rows, the only box shape that yields this
+// layout, fetched whole 32-byte sectors and issued one request per row,
+// which measured slower.  Roles: warps 0-2 copy the halo (warp 0 also loads
+// the weights by TMA), warp 3 issues the MMAs, warps 4-7 run the epilogue;
+// every wait is bounded.
 constexpr int BAND_PX = TC_M + 2;   // halo pixels per row
-constexpr int BAND_THREADS = 192;
+constexpr int BAND_THREADS = 256;
+constexpr int BAND_PRODUCERS = 96;  // threads of warps 0-2
 
 struct BandArgs {
     int n, h, w, nchunk0, nchunk, cout, R, stages;
@@ -195,12 +201,19 @@ struct BandArgs {
     uint32_t acc_row;      // TMEM columns per output row (power of two >= cout)
     uint32_t acc_cols;     // TMEM columns of one accumulator buffer (R * acc_row)
     uint32_t tmem_cols;
+    const __nv_bfloat16 *x0, *x1;  // NHWC inputs with c0 / c1 channels per pixel
+    int c0, c1;
     const float *bias;
     void *y;
     long long ys;
     int relu;
     int *err;
 };
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 
 // Shared-memory descriptor of an unswizzled K-major operand: core matrices
 // (8 rows x 16 B) `sbo` bytes apart along M/N and `lbo` bytes apart along K.
@@ -210,8 +223,7 @@ __device__ __forceinline__ uint64_t sdesc_nosw(uint32_t addr, uint32_t lbo, uint
 }
 
 __global__ void __launch_bounds__(BAND_THREADS, 1)
-k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-               const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
+k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ntile_w = 9 * a.nchunk;
@@ -229,7 +241,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     if (threadIdx.x < a.cout) sbias[threadIdx.x] = a.bias[threadIdx.x];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], BAND_PRODUCERS);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&wfull, 1);
@@ -240,44 +252,57 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(&tmem_base, a.tmem_cols);
+    if (warp == 3) tmem_alloc(&tmem_base, a.tmem_cols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
 
-    if (warp == 0) {
-        if (lane == 0) {
+    if (warp < 3) {
+        const int ptid = threadIdx.x;
+        if (ptid == 0) {
             mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
             for (int tap = 0; tap < 9; ++tap)
                 for (int ch = 0; ch < a.nchunk; ++ch)
                     tma_load_3d(sW + size_t(tap * a.nchunk + ch) * a.wtile, &mapB, &wfull, ch * TC_KC, 0, tap);
-            long long i = 0;
-            bool go = true;
-            for (long long band = blockIdx.x; band < a.nbands && go; band += gridDim.x) {
-                const int bx = int(band % a.nbx);
-                const long long rest = band / a.nbx;
-                const int by = int(rest % a.nby), img = int(rest / a.nby);
-                const int x0 = bx * TC_M, y0 = by * a.R;
-                for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
-                    const int s = int(i % S);
-                    const long long use = i / S;
-                    if (use > 0 && !mbar_wait(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 11)) {
-                        go = false;
-                        break;
-                    }
-                    mbar_expect_tx(&full[s], a.tx_bytes);
-                    uint8_t *dst = sA + size_t(s) * a.stage_bytes;
-                    const bool first = ch < a.nchunk0;
-                    const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
-#pragma unroll
-                    for (int blk = 0; blk < 4; ++blk)
-                        tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
-                                    x0 - 1, y0 - 1, img);
+        }
+        const int per_stage = (a.R + 2) * BAND_PX * 4;  // 16-byte copies
+        long long i = 0;
+        bool go = true;
+        for (long long band = blockIdx.x; band < a.nbands && go; band += gridDim.x) {
+            const int bx = int(band % a.nbx);
+            const long long rest = band / a.nbx;
+            const int by = int(rest % a.nby), img = int(rest / a.nby);
+            const int x0 = bx * TC_M, y0 = by * a.R;
+            for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
+                const int s = int(i % S);
+                const long long use = i / S;
+                if (use > 0 && !mbar_wait(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 11)) {
+                    go = false;
+                    break;
                 }
+                const bool first = ch < a.nchunk0;
+                const __nv_bfloat16 *src = first ? a.x0 : a.x1;
+                const int C = first ? a.c0 : a.c1;
+                const int cb = (first ? ch : ch - a.nchunk0) * TC_KC;
+                uint8_t *dst = sA + size_t(s) * a.stage_bytes;
+                for (int j = ptid; j < per_stage; j += BAND_PRODUCERS) {
+                    const int blk = j & 3, rp = j >> 2;
+                    const int row = rp / BAND_PX, px = rp - row * BAND_PX;
+                    const int gy = y0 - 1 + row, gx = x0 - 1 + px;
+                    const bool v = gy >= 0 && gy < a.h && gx >= 0 && gx < a.w;
+                    const __nv_bfloat16 *g =
+                        v ? src + ((((long long)img * a.h + gy) * a.w + gx) * C + cb + blk * 8) : src;
+                    cp_async16(dst + blk * a.blk_stride + rp * 16, g, v ? 16u : 0u);
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+                // the MMA reads the halo through the async proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
             }
         }
-    } else if (warp == 1) {
+    } else if (warp == 3) {
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(a.cout);
             bool ok = mbar_wait(&wfull, 0, &abort_flag, a.err, 12);
@@ -376,7 +401,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 3) {
         tc_fence_after();
         tmem_dealloc(tmem, a.tmem_cols);
     }
@@ -499,18 +524,6 @@ bool map_act(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int tw
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// NHWC BF16 activations for the band kernel: dims (channels, w, h, n), box
-// (8 channels, 130 pixels, R + 2 rows, 1), no swizzle.
-bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int R) {
-    const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
-    const cuuint64_t strides[3] = {cuuint64_t(c) * 2, cuuint64_t(c) * 2 * w, cuuint64_t(c) * 2 * w * h};
-    const cuuint32_t box[4] = {8, cuuint32_t(BAND_PX), cuuint32_t(R + 2), 1};
-    const cuuint32_t es[4] = {1, 1, 1, 1};
-    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box, es,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // 0 = choose per layer, 1 = tile kernel only, 2 = band kernel where it
 // applies (glbm_nn_tc_set_variant).
 int g_tc_variant = 0;
@@ -551,11 +564,11 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
 glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
                         const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
                         int R, int stages, size_t smem) {
-    CUtensorMap mA0, mA1;
-    if (!map_act_band(&mA0, x0, c0, w, h, n, R) ||
-        !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, R))
-        return tcfail(GLBM_EINVAL, "nn_tc_conv: band activation tensor map rejected");
     BandArgs a;
+    a.x0 = static_cast<const __nv_bfloat16 *>(x0);
+    a.x1 = static_cast<const __nv_bfloat16 *>(c1 > 0 ? x1 : x0);
+    a.c0 = c0;
+    a.c1 = c1 > 0 ? c1 : c0;
     a.n = n;
     a.h = h;
     a.w = w;
@@ -589,7 +602,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: device query");
     const long long grid = a.nbands < nsm ? a.nbands : nsm;
-    k_tc_conv_band<<<unsigned(grid), BAND_THREADS, smem, st>>>(mA0, mA1, mB, a);
+    k_tc_conv_band<<<unsigned(grid), BAND_THREADS, smem, st>>>(mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (band)");
 }
