@@ -491,9 +491,11 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
  * pixels and <= 64 output channels whose weights fit shared memory run the
  * band kernel (weights resident, each band's halo loaded once per 32-channel
- * chunk); the rest run the tile kernel (one 128-pixel tile per CTA, one TMA
- * tile per tap); 1 = tile kernel always; 2 = as 0 (band where it applies).
- * Both compute the same convolution; other values reset to 0. */
+ * chunk; with 32 output channels the three vertical taps are stacked into
+ * one MMA of 96 columns); the rest run the tile kernel (one 128-pixel tile
+ * per CTA, one TMA tile per tap); 1 = tile kernel always; 2 = as 0; 3 = band
+ * kernel where it applies but never stacked.  All compute the same
+ * convolution; other values reset to 0. */
 void glbm_nn_tc_set_variant(int variant);
 
 /* FP32 [cout][cin][ksize][ksize] -> BF16 [ksize^2][cout_pad][cin_pad] (the

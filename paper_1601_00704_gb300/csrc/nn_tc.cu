@@ -203,12 +203,23 @@ struct BandArgs {
     uint32_t tmem_cols;
     const __nv_bfloat16 *x0, *x1;  // NHWC inputs with c0 / c1 channels per pixel
     int c0, c1;
+    int stack;  // 1: the three dy taps stacked along N (see k_tc_conv_band)
     const float *bias;
     void *y;
     long long ys;
     int relu;
     int *err;
 };
+
+// 16 zero FP32 columns into this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
@@ -257,6 +268,16 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
+    if (a.stack) {
+        // stacked MMAs always accumulate: both buffers start from zero (the
+        // epilogue zeroes a buffer again after reading it)
+        if (warp >= 4)
+            for (uint32_t c = 0; c < 2 * a.acc_cols; c += 16) tmem_zero16(tmem + c + (uint32_t((warp & 3) * 32) << 16));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
 
     if (warp < 3) {
         const int ptid = threadIdx.x;
@@ -264,7 +285,9 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
             mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
             for (int tap = 0; tap < 9; ++tap)
                 for (int ch = 0; ch < a.nchunk; ++ch)
-                    tma_load_3d(sW + size_t(tap * a.nchunk + ch) * a.wtile, &mapB, &wfull, ch * TC_KC, 0, tap);
+                    tma_load_3d(sW + size_t(a.stack ? ((ch * 3 + tap % 3) * 3 + (2 - tap / 3)) : (tap * a.nchunk + ch)) *
+                                         a.wtile,
+                                &mapB, &wfull, ch * TC_KC, 0, tap);
         }
         const int per_stage = (a.R + 2) * BAND_PX * 4;  // 16-byte copies
         long long i = 0;
@@ -304,7 +327,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
         }
     } else if (warp == 3) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(a.cout);
+            const uint32_t idesc = idesc_bf16(a.stack ? 3 * a.cout : a.cout);
             bool ok = mbar_wait(&wfull, 0, &abort_flag, a.err, 12);
             tc_fence_after();
             long long i = 0, t = 0;
@@ -325,6 +348,26 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(sA + size_t(s) * a.stage_bytes);
+                    if (a.stack) {
+                        // N = 3 cout: B stacks the weights of dy = +1, 0, -1 for one dx, so
+                        // one MMA on halo row i adds to output rows i-2, i-1, i, whose
+                        // accumulator slots (row + 2) are contiguous: D = acc + i cout.
+                        const uint64_t a0 = sdesc_nosw(base, a.blk_stride, 128u);
+                        const uint64_t b0 = sdesc_k64(sW + size_t(ch * 9) * a.wtile);
+                        const uint32_t bstep = (3 * a.wtile) >> 4, kstep = (2 * a.blk_stride) >> 4;
+                        for (int hr = 0; hr < a.R + 2; ++hr) {
+                            const uint32_t d = acc + uint32_t(hr * a.cout);
+                            const uint64_t arow = a0 + uint64_t(hr * BAND_PX);  // 16-byte units
+#pragma unroll
+                            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk)
+                                    umma_bf16(d, arow + uint64_t(dxi + kk * kstep),
+                                              b0 + uint64_t(dxi * bstep + kk * 2), idesc, 1u);
+                        }
+                        umma_commit(&empty[s]);
+                        continue;
+                    }
                     for (int tap = 0; tap < 9; ++tap) {
                         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
                         const uint64_t bd = sdesc_k64(sW + size_t(tap * a.nchunk + ch) * a.wtile);
@@ -366,8 +409,8 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
                 const int py = by * a.R + r;
                 for (int c = 0; c < a.cout; c += 16) {
                     float v[16];
-                    tmem_ld16(tmem + uint32_t(ab) * a.acc_cols + uint32_t(r) * a.acc_row + uint32_t(c) +
-                                  (uint32_t(q * 32) << 16),
+                    tmem_ld16(tmem + uint32_t(ab) * a.acc_cols + uint32_t(a.stack ? r + 2 : r) * a.acc_row +
+                                  uint32_t(c) + (uint32_t(q * 32) << 16),
                               v);
                     uint32_t pk[8];
 #pragma unroll
@@ -393,6 +436,11 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
                     }
                 }
                 __syncwarp();
+            }
+            if (a.stack) {
+                for (uint32_t c = 0; c < a.acc_cols; c += 16)
+                    tmem_zero16(tmem + uint32_t(ab) * a.acc_cols + c + (uint32_t(q * 32) << 16));
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
             __syncwarp();
@@ -535,13 +583,17 @@ constexpr size_t kBandMaxWeights = 80 * 1024;  // larger weight sets: tile kerne
 // Band kernel plan for a layer: rows per band and ring stages, or false when
 // the layer does not fit it (3x3, BF16 output, rows of >= 128 pixels,
 // cout <= 64, resident weights and two or more stages in shared memory).
-bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem) {
+bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem,
+               int *stack) {
     if (k != 3 || f32_nchw || w < TC_M || cout > 64) return false;
     const size_t wbytes = size_t(9) * (cin / TC_KC) * cout * TC_KC * 2;
     if (wbytes > kBandMaxWeights) return false;
     int row = 32;
     while (row < cout) row <<= 1;
-    int r = 256 / row;  // two accumulator buffers of r rows fill at most 512 columns
+    // 32 output channels: stack the three dy taps (N = 96); two buffers of
+    // R + 4 row slots x 32 columns fill 512 columns at R = 4
+    *stack = (cout == 32 && g_tc_variant != 3) ? 1 : 0;
+    int r = *stack ? 4 : 256 / row;  // two accumulator buffers fill at most 512 columns
     if (r > 8) r = 8;
     if (r > h) r = h;
     for (; r >= 1; --r) {
@@ -563,7 +615,7 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
 
 glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
                         const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
-                        int R, int stages, size_t smem) {
+                        int R, int stages, size_t smem, int stack) {
     BandArgs a;
     a.x0 = static_cast<const __nv_bfloat16 *>(x0);
     a.x1 = static_cast<const __nv_bfloat16 *>(c1 > 0 ? x1 : x0);
@@ -584,9 +636,12 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     a.stage_bytes = 4 * a.blk_stride;
     a.tx_bytes = uint32_t(4 * (R + 2) * BAND_PX * 16);
     a.wtile = uint32_t(cout * TC_KC * 2);
+    a.stack = stack;
     a.acc_row = 32;
     while (a.acc_row < uint32_t(cout)) a.acc_row <<= 1;
-    a.acc_cols = uint32_t(R) * a.acc_row;
+    // stacked: row slots -2 .. R + 1, exactly cout columns apart
+    a.acc_cols = stack ? uint32_t(R + 4) * uint32_t(cout) : uint32_t(R) * a.acc_row;
+    if (stack) a.acc_row = uint32_t(cout);
     a.tmem_cols = 32;
     while (a.tmem_cols < 2 * a.acc_cols) a.tmem_cols <<= 1;
     a.bias = bias;
@@ -609,7 +664,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 
 }  // namespace
 
-extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 2) ? variant : 0; }
+extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 3) ? variant : 0; }
 
 extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, int k,
                                        const void *wt, const float *bias, int cout, void *y, long long ys, int relu,
@@ -652,9 +707,10 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     }
     int R = 0, stages = 0;
     size_t bsmem = 0;
-    if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem))
+    int stack = 0;
+    if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem, &stack))
         return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
-                           static_cast<cudaStream_t>(stream), R, stages, bsmem);
+                           static_cast<cudaStream_t>(stream), R, stages, bsmem, stack);
     TcConvArgs a;
     a.n = n;
     a.h = h;

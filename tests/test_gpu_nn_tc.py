@@ -55,11 +55,13 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 0])
+@pytest.mark.parametrize("variant", [1, 0, 3])
 @pytest.mark.parametrize("n,h,w,c0,c1,cout,k,relu,head", CASES)
 def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head, variant):
-    """Every case on the tile kernel (variant 1) and with the per-layer
-    choice (variant 0: the band kernel wherever it applies)."""
+    """Every case on the tile kernel (variant 1), with the per-layer choice
+    (variant 0: the band kernel wherever it applies, with the dy taps
+    stacked along N for 32 output channels) and with the band kernel
+    unstacked (variant 3)."""
     import torch
     lib = pkg.load()
     lib.glbm_nn_tc_set_variant(variant)
