@@ -489,7 +489,7 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
 
 /* Choice of tensor-core convolution kernel for glbm_nn_tc_conv (process-wide):
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
- * pixels and <= 64 output channels whose weights fit shared memory run the
+ * pixels and 32 or 64 output channels whose weights fit shared memory run the
  * band kernel (weights resident, each band's halo loaded once per 32-channel
  * chunk; with 32 output channels the three vertical taps are stacked into
  * one MMA of 96 columns); the rest run the tile kernel (one 128-pixel tile

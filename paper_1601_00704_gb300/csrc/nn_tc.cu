@@ -179,16 +179,17 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 // ((r+1+dy) * 130 + 1+dx) * 16 bytes in: core matrices of 8 pixels are 128 B
 // apart along M (SBO) and 8-channel blocks one block stride apart along K
 // (LBO).  Each band accumulates R rows into one of two TMEM buffers, so the
-// epilogue of one band overlaps the MMAs of the next.  The halo is copied by
-// three producer warps with 16-byte cp.async (zero-filled outside the
-// image): a TMA box with 16-byte rows, the only box shape that yields this
-// layout, fetched whole 32-byte sectors and issued one request per row,
-// which measured slower.  Roles: warps 0-2 copy the halo (warp 0 also loads
-// the weights by TMA), warp 3 issues the MMAs, warps 4-7 run the epilogue;
-// every wait is bounded.
+// epilogue of one band overlaps the MMAs of the next.  The halo arrives by
+// TMA, one box of 8 channels x 130 pixels x (R + 2) rows per 8-channel block
+// (zero fill outside the image is the padding).  With 32 output channels the
+// three vertical taps are stacked along N: one MMA of 96 columns per halo
+// row, horizontal tap and 16 channels feeds three output rows' accumulator
+// slots at once (the slots are zeroed by the epilogue after it reads them).
+// Roles: warp 0 issues TMA, warp 3 the MMAs, warps 4-7 run the epilogue
+// (warps 1-2 idle: the TMEM lane quarters fix the epilogue to warps whose
+// index is 0-3 mod 4); every wait is bounded.
 constexpr int BAND_PX = TC_M + 2;   // halo pixels per row
 constexpr int BAND_THREADS = 256;
-constexpr int BAND_PRODUCERS = 96;  // threads of warps 0-2
 
 struct BandArgs {
     int n, h, w, nchunk0, nchunk, cout, R, stages;
@@ -211,19 +212,31 @@ struct BandArgs {
     int *err;
 };
 
-// 16 zero FP32 columns into this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+// 32 zero FP32 columns into this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
     const uint32_t z = 0u;
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-        "%1};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
         "r"(z)
         : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
+// 32 consecutive FP32 columns of this thread's TMEM lane (one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // Shared-memory descriptor of an unswizzled K-major operand: core matrices
@@ -234,13 +247,13 @@ __device__ __forceinline__ uint64_t sdesc_nosw(uint32_t addr, uint32_t lbo, uint
 }
 
 __global__ void __launch_bounds__(BAND_THREADS, 1)
-k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
+k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+               const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ntile_w = 9 * a.nchunk;
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(ntile_w) * a.wtile;
-    uint8_t *sO = sA + size_t(a.stages) * a.stage_bytes;  // epilogue staging, 4 warps x 32 pixels x cout
     constexpr int SMAX = 3;
     __shared__ __align__(8) uint64_t full[SMAX], empty[SMAX], wfull, accfull[2], accempty[2];
     __shared__ uint32_t tmem_base;
@@ -252,7 +265,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
     if (threadIdx.x < a.cout) sbias[threadIdx.x] = a.bias[threadIdx.x];
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], BAND_PRODUCERS);
+            mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         mbar_init(&wfull, 1);
@@ -272,57 +285,44 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
         // stacked MMAs always accumulate: both buffers start from zero (the
         // epilogue zeroes a buffer again after reading it)
         if (warp >= 4)
-            for (uint32_t c = 0; c < 2 * a.acc_cols; c += 16) tmem_zero16(tmem + c + (uint32_t((warp & 3) * 32) << 16));
+            for (uint32_t c = 0; c < 2 * a.acc_cols; c += 32) tmem_zero32(tmem + c + (uint32_t((warp & 3) * 32) << 16));
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
     }
 
-    if (warp < 3) {
-        const int ptid = threadIdx.x;
-        if (ptid == 0) {
+    if (warp == 0) {
+        if (lane == 0) {
             mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
             for (int tap = 0; tap < 9; ++tap)
                 for (int ch = 0; ch < a.nchunk; ++ch)
                     tma_load_3d(sW + size_t(a.stack ? ((ch * 3 + tap % 3) * 3 + (2 - tap / 3)) : (tap * a.nchunk + ch)) *
                                          a.wtile,
                                 &mapB, &wfull, ch * TC_KC, 0, tap);
-        }
-        const int per_stage = (a.R + 2) * BAND_PX * 4;  // 16-byte copies
-        long long i = 0;
-        bool go = true;
-        for (long long band = blockIdx.x; band < a.nbands && go; band += gridDim.x) {
-            const int bx = int(band % a.nbx);
-            const long long rest = band / a.nbx;
-            const int by = int(rest % a.nby), img = int(rest / a.nby);
-            const int x0 = bx * TC_M, y0 = by * a.R;
-            for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
-                const int s = int(i % S);
-                const long long use = i / S;
-                if (use > 0 && !mbar_wait(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 11)) {
-                    go = false;
-                    break;
+            long long i = 0;
+            bool go = true;
+            for (long long band = blockIdx.x; band < a.nbands && go; band += gridDim.x) {
+                const int bx = int(band % a.nbx);
+                const long long rest = band / a.nbx;
+                const int by = int(rest % a.nby), img = int(rest / a.nby);
+                const int x0 = bx * TC_M, y0 = by * a.R;
+                for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
+                    const int s = int(i % S);
+                    const long long use = i / S;
+                    if (use > 0 && !mbar_wait(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 11)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], a.tx_bytes);
+                    uint8_t *dst = sA + size_t(s) * a.stage_bytes;
+                    const bool first = ch < a.nchunk0;
+                    const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
+#pragma unroll
+                    for (int blk = 0; blk < 4; ++blk)
+                        tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
+                                    x0 - 1, y0 - 1, img);
                 }
-                const bool first = ch < a.nchunk0;
-                const __nv_bfloat16 *src = first ? a.x0 : a.x1;
-                const int C = first ? a.c0 : a.c1;
-                const int cb = (first ? ch : ch - a.nchunk0) * TC_KC;
-                uint8_t *dst = sA + size_t(s) * a.stage_bytes;
-                for (int j = ptid; j < per_stage; j += BAND_PRODUCERS) {
-                    const int blk = j & 3, rp = j >> 2;
-                    const int row = rp / BAND_PX, px = rp - row * BAND_PX;
-                    const int gy = y0 - 1 + row, gx = x0 - 1 + px;
-                    const bool v = gy >= 0 && gy < a.h && gx >= 0 && gx < a.w;
-                    const __nv_bfloat16 *g =
-                        v ? src + ((((long long)img * a.h + gy) * a.w + gx) * C + cb + blk * 8) : src;
-                    cp_async16(dst + blk * a.blk_stride + rp * 16, g, v ? 16u : 0u);
-                }
-                asm volatile("cp.async.commit_group;" ::: "memory");
-                asm volatile("cp.async.wait_group 0;" ::: "memory");
-                // the MMA reads the halo through the async proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[s])) : "memory");
             }
         }
     } else if (warp == 3) {
@@ -389,13 +389,9 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
             }
         }
     } else {
-        // Epilogue: per output row, each lane converts its pixel's cout
-        // channels and parks them in this warp's staging slot (32 pixels x
-        // cout BF16); the warp then writes the 32 pixels with 16-byte stores
-        // that are contiguous across lanes.
+        // Epilogue: per output row one TMEM load of the pixel's channels (32
+        // columns per load, one wait), bias, ReLU, BF16, 16-byte stores.
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
-        const int c8 = a.cout / 8;  // 16-byte chunks per pixel
-        uint4 *so = reinterpret_cast<uint4 *>(sO + size_t(q) * 32 * a.cout * 2);
         long long t = 0;
         for (long long band = blockIdx.x; band < a.nbands; band += gridDim.x, ++t) {
             const int ab = int(t & 1);
@@ -404,42 +400,39 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapB, const BandArgs a) {
             const int bx = int(band % a.nbx);
             const long long rest = band / a.nbx;
             const int by = int(rest % a.nby), img = int(rest / a.nby);
-            const int px0 = bx * TC_M + q * 32;  // this warp's first pixel
+            const int px = bx * TC_M + q * 32 + lane;
             for (int r = 0; r < a.R; ++r) {
                 const int py = by * a.R + r;
-                for (int c = 0; c < a.cout; c += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + uint32_t(ab) * a.acc_cols + uint32_t(a.stack ? r + 2 : r) * a.acc_row +
-                                  uint32_t(c) + (uint32_t(q * 32) << 16),
-                              v);
-                    uint32_t pk[8];
+                const bool ok = px < a.w && py < a.h;
+                const uint32_t col = tmem + uint32_t(ab) * a.acc_cols + uint32_t(a.stack ? r + 2 : r) * a.acc_row +
+                                     (uint32_t(q * 32) << 16);
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
+                                                       (((long long)img * a.h + py) * a.w + px) * a.ys);
+                for (int c = 0; c < a.cout; c += 32) {
+                    float v[32];
+                    tmem_ld32(col + uint32_t(c), v);
+                    if (!ok) continue;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float lo = v[2 * j] + sbias[c + 2 * j], hi = v[2 * j + 1] + sbias[c + 2 * j + 1];
-                        if (a.relu) {
-                            lo = fmaxf(lo, 0.0f);
-                            hi = fmaxf(hi, 0.0f);
+                    for (int j4 = 0; j4 < 4; ++j4) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int cc = j4 * 8 + 2 * j;
+                            float lo = v[cc] + sbias[c + cc], hi = v[cc + 1] + sbias[c + cc + 1];
+                            if (a.relu) {
+                                lo = fmaxf(lo, 0.0f);
+                                hi = fmaxf(hi, 0.0f);
+                            }
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
+                            pk[j] = *reinterpret_cast<uint32_t *>(&b2);
                         }
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-                        pk[j] = *reinterpret_cast<uint32_t *>(&b2);
-                    }
-                    so[lane * c8 + c / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    so[lane * c8 + c / 8 + 1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
-                __syncwarp();
-                if (py < a.h) {
-                    __nv_bfloat16 *yrow = static_cast<__nv_bfloat16 *>(a.y) + (((long long)img * a.h + py) * a.w) * a.ys;
-                    for (int u = lane; u < 32 * c8; u += 32) {
-                        const int p = u / c8, ch = u - p * c8;
-                        if (px0 + p < a.w)
-                            *reinterpret_cast<uint4 *>(yrow + (long long)(px0 + p) * a.ys + ch * 8) = so[u];
+                        dst[c / 8 + j4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 }
-                __syncwarp();
             }
             if (a.stack) {
-                for (uint32_t c = 0; c < a.acc_cols; c += 16)
-                    tmem_zero16(tmem + uint32_t(ab) * a.acc_cols + c + (uint32_t(q * 32) << 16));
+                for (uint32_t c = 0; c < a.acc_cols; c += 32)
+                    tmem_zero32(tmem + uint32_t(ab) * a.acc_cols + c + (uint32_t(q * 32) << 16));
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
@@ -572,6 +565,18 @@ bool map_act(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int tw
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// NHWC BF16 activations for the band kernel: dims (channels, w, h, n), box
+// (8 channels, 130 pixels, R + 2 rows, 1), no swizzle.
+bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, int R) {
+    const cuuint64_t dims[4] = {cuuint64_t(c), cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
+    const cuuint64_t strides[3] = {cuuint64_t(c) * 2, cuuint64_t(c) * 2 * w, cuuint64_t(c) * 2 * w * h};
+    const cuuint32_t box[4] = {8, cuuint32_t(BAND_PX), cuuint32_t(R + 2), 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(ptr), dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // 0 = choose per layer, 1 = tile kernel only, 2 = band kernel where it
 // applies (glbm_nn_tc_set_variant).
 int g_tc_variant = 0;
@@ -585,7 +590,7 @@ constexpr size_t kBandMaxWeights = 80 * 1024;  // larger weight sets: tile kerne
 // cout <= 64, resident weights and two or more stages in shared memory).
 bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem,
                int *stack) {
-    if (k != 3 || f32_nchw || w < TC_M || cout > 64) return false;
+    if (k != 3 || f32_nchw || w < TC_M || cout > 64 || cout % 32) return false;
     const size_t wbytes = size_t(9) * (cin / TC_KC) * cout * TC_KC * 2;
     if (wbytes > kBandMaxWeights) return false;
     int row = 32;
@@ -599,9 +604,8 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
     for (; r >= 1; --r) {
         const size_t blk = (size_t(r + 2) * BAND_PX * 16 + 127) / 128 * 128;
         const size_t stage = 4 * blk;
-        const size_t staging = size_t(4) * 32 * cout * 2;
         for (int st = 3; st >= 2; --st) {
-            const size_t total = 1024 + wbytes + st * stage + staging;
+            const size_t total = 1024 + wbytes + st * stage;
             if (total <= kSmemLimit) {
                 *R = r;
                 *stages = st;
@@ -616,6 +620,10 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
 glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
                         const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
                         int R, int stages, size_t smem, int stack) {
+    CUtensorMap mA0, mA1;
+    if (!map_act_band(&mA0, x0, c0, w, h, n, R) ||
+        !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, R))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: band activation tensor map rejected");
     BandArgs a;
     a.x0 = static_cast<const __nv_bfloat16 *>(x0);
     a.x1 = static_cast<const __nv_bfloat16 *>(c1 > 0 ? x1 : x0);
@@ -657,7 +665,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: device query");
     const long long grid = a.nbands < nsm ? a.nbands : nsm;
-    k_tc_conv_band<<<unsigned(grid), BAND_THREADS, smem, st>>>(mB, a);
+    k_tc_conv_band<<<unsigned(grid), BAND_THREADS, smem, st>>>(mA0, mA1, mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (band)");
 }
