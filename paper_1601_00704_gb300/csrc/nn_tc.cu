@@ -388,7 +388,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 umma_commit(&accfull[ab]);
             }
         }
-    } else {
+    } else if (warp >= 4) {
         // Epilogue: per output row one TMEM load of the pixel's channels (32
         // columns per load, one wait), bias, ReLU, BF16, 16-byte stores.
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp

@@ -52,6 +52,8 @@ CASES = [
     (2, 16, 128, 32, 0, 32, 3, True, False),    # one pixel tile per row, two images
     (1, 12, 300, 32, 32, 64, 3, False, False),  # 4-row bands, a 44-pixel last tile
     (1, 8, 2048, 32, 0, 32, 3, True, False),    # one band of 8 rows across 16 pixel tiles
+    (1, 640, 128, 32, 0, 32, 3, True, False),   # 160 bands: CTAs reuse both accumulator buffers (stacked)
+    (1, 640, 128, 32, 0, 64, 3, False, False),  # 160 bands, 64 output channels (unstacked)
 ]
 
 
