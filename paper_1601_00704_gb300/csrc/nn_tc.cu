@@ -184,7 +184,8 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 // (zero fill outside the image is the padding).  With 32 output channels the
 // three vertical taps are stacked along N: one MMA of 96 columns per halo
 // row, horizontal tap and 16 channels feeds three output rows' accumulator
-// slots at once (the slots are zeroed by the epilogue after it reads them).
+// slots at once (each band first clears its slots with MMAs of an all-zero
+// A operand and accumulate = 0).
 // Roles: warp 0 issues TMA, warp 3 the MMAs, warps 4-7 run the epilogue
 // (warps 1-2 idle: the TMEM lane quarters fix the epilogue to warps whose
 // index is 0-3 mod 4); every wait is bounded.
@@ -212,31 +213,17 @@ struct BandArgs {
     int *err;
 };
 
-// 32 zero FP32 columns into this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
-    const uint32_t z = 0u;
+// Two groups of 32 consecutive FP32 columns of this thread's TMEM lane,
+// both loads in flight before one wait (the values are outputs of the same
+// statement, so nothing reads them early).
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float (&v0)[32], float (&v1)[32]) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
-        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
-        "r"(z)
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=f"(v0[0]), "=f"(v0[1]), "=f"(v0[2]), "=f"(v0[3]), "=f"(v0[4]), "=f"(v0[5]), "=f"(v0[6]), "=f"(v0[7]), "=f"(v0[8]), "=f"(v0[9]), "=f"(v0[10]), "=f"(v0[11]), "=f"(v0[12]), "=f"(v0[13]), "=f"(v0[14]), "=f"(v0[15]), "=f"(v0[16]), "=f"(v0[17]), "=f"(v0[18]), "=f"(v0[19]), "=f"(v0[20]), "=f"(v0[21]), "=f"(v0[22]), "=f"(v0[23]), "=f"(v0[24]), "=f"(v0[25]), "=f"(v0[26]), "=f"(v0[27]), "=f"(v0[28]), "=f"(v0[29]), "=f"(v0[30]), "=f"(v0[31]), "=f"(v1[0]), "=f"(v1[1]), "=f"(v1[2]), "=f"(v1[3]), "=f"(v1[4]), "=f"(v1[5]), "=f"(v1[6]), "=f"(v1[7]), "=f"(v1[8]), "=f"(v1[9]), "=f"(v1[10]), "=f"(v1[11]), "=f"(v1[12]), "=f"(v1[13]), "=f"(v1[14]), "=f"(v1[15]), "=f"(v1[16]), "=f"(v1[17]), "=f"(v1[18]), "=f"(v1[19]), "=f"(v1[20]), "=f"(v1[21]), "=f"(v1[22]), "=f"(v1[23]), "=f"(v1[24]), "=f"(v1[25]), "=f"(v1[26]), "=f"(v1[27]), "=f"(v1[28]), "=f"(v1[29]), "=f"(v1[30]), "=f"(v1[31])
+        : "r"(ta), "r"(tb)
         : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane (one wait).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // Shared-memory descriptor of an unswizzled K-major operand: core matrices
@@ -260,9 +247,15 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     __shared__ volatile int abort_flag;
     __shared__ float sbias[64];
 
+    // an all-zero A operand (128 rows x 16 K, unswizzled): MMAs with it and
+    // accumulate = 0 clear the stacked accumulator slots of a band
+    __shared__ __align__(128) uint8_t szero[4096];
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = a.stages;
     if (threadIdx.x < a.cout) sbias[threadIdx.x] = a.bias[threadIdx.x];
+    for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -281,16 +274,6 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    if (a.stack) {
-        // stacked MMAs always accumulate: both buffers start from zero (the
-        // epilogue zeroes a buffer again after reading it)
-        if (warp >= 4)
-            for (uint32_t c = 0; c < 2 * a.acc_cols; c += 32) tmem_zero32(tmem + c + (uint32_t((warp & 3) * 32) << 16));
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    }
 
     if (warp == 0) {
         if (lane == 0) {
@@ -340,6 +323,18 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 }
                 tc_fence_after();
                 const uint32_t acc = tmem + uint32_t(ab) * a.acc_cols;
+                if (a.stack) {
+                    // clear the band's slots: zero A times any finite B, accumulate = 0,
+                    // windows of 3 cout columns covering [0, acc_cols)
+                    const uint64_t z = sdesc_nosw(smem_u32(szero), 2048u, 128u);
+                    const uint64_t bw = sdesc_k64(sW);
+                    const uint32_t n3 = uint32_t(3 * a.cout);
+                    for (uint32_t c0 = 0;; c0 += n3) {
+                        const uint32_t c = c0 + n3 > a.acc_cols ? a.acc_cols - n3 : c0;
+                        umma_bf16(acc + c, z, bw, idesc, 0u);
+                        if (c0 + n3 >= a.acc_cols) break;
+                    }
+                }
                 for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
                     const int s = int(i % S);
                     if (!mbar_wait(&full[s], uint32_t(i / S) & 1u, &abort_flag, a.err, 14)) {
@@ -401,24 +396,37 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             const long long rest = band / a.nbx;
             const int by = int(rest % a.nby), img = int(rest / a.nby);
             const int px = bx * TC_M + q * 32 + lane;
-            for (int r = 0; r < a.R; ++r) {
-                const int py = by * a.R + r;
-                const bool ok = px < a.w && py < a.h;
-                const uint32_t col = tmem + uint32_t(ab) * a.acc_cols + uint32_t(a.stack ? r + 2 : r) * a.acc_row +
-                                     (uint32_t(q * 32) << 16);
-                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
-                                                       (((long long)img * a.h + py) * a.w + px) * a.ys);
-                for (int c = 0; c < a.cout; c += 32) {
-                    float v[32];
-                    tmem_ld32(col + uint32_t(c), v);
-                    if (!ok) continue;
+            // two 32-column groups per TMEM wait: two rows of 32 channels, or
+            // one row of 64
+            const uint32_t lanes = uint32_t(q * 32) << 16;
+            const uint32_t buf = tmem + uint32_t(ab) * a.acc_cols + lanes;
+            const int first_slot = a.stack ? 2 : 0;
+            const int ngroups = a.R * (a.cout / 32);
+            for (int g = 0; g < ngroups; g += 2) {
+                float v[2][32];
+                int rr[2], cc0[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int gg = g + u < ngroups ? g + u : g;  // an odd last group loads twice
+                    rr[u] = gg / (a.cout / 32);
+                    cc0[u] = (gg % (a.cout / 32)) * 32;
+                }
+                tmem_ld32x2(buf + uint32_t(rr[0] + first_slot) * a.acc_row + uint32_t(cc0[0]),
+                            buf + uint32_t(rr[1] + first_slot) * a.acc_row + uint32_t(cc0[1]), v[0], v[1]);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (g + u >= ngroups) break;
+                    const int py = by * a.R + rr[u];
+                    if (px >= a.w || py >= a.h) continue;
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
+                                                           (((long long)img * a.h + py) * a.w + px) * a.ys + cc0[u]);
 #pragma unroll
                     for (int j4 = 0; j4 < 4; ++j4) {
                         uint32_t pk[4];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const int cc = j4 * 8 + 2 * j;
-                            float lo = v[cc] + sbias[c + cc], hi = v[cc + 1] + sbias[c + cc + 1];
+                            float lo = v[u][cc] + sbias[cc0[u] + cc], hi = v[u][cc + 1] + sbias[cc0[u] + cc + 1];
                             if (a.relu) {
                                 lo = fmaxf(lo, 0.0f);
                                 hi = fmaxf(hi, 0.0f);
@@ -426,14 +434,9 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                             __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
                             pk[j] = *reinterpret_cast<uint32_t *>(&b2);
                         }
-                        dst[c / 8 + j4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[j4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 }
-            }
-            if (a.stack) {
-                for (uint32_t c = 0; c < a.acc_cols; c += 32)
-                    tmem_zero32(tmem + uint32_t(ab) * a.acc_cols + c + (uint32_t(q * 32) << 16));
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
             __syncwarp();
