@@ -487,6 +487,29 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
                             long long ys, int relu, int f32_nchw,
                             int cout_store, int *err, void *stream);
 
+/*
+ * The band kernel of a 3x3 convolution with 32 output channels (as in
+ * glbm_nn_tc_conv, bias and ReLU applied) with outputs fused into its
+ * epilogue, so that the layers that follow need no pass of their own:
+ *   y       BF16 NHWC output (pixel stride ys), or NULL when only the fused
+ *           outputs are wanted;
+ *   pool_y  if not NULL, the 2x2 average of the BF16 output, BF16 NHWC
+ *           (n, h/2, w/2, 32), computed as glbm_nn_pool2_nhwc does (h, w
+ *           even);
+ *   head_y  if not NULL, a 1x1 convolution (the network's head) of the BF16
+ *           output: head_w BF16 [head_out][32], head_b FP32 [head_out],
+ *           head_out in 1..4, written FP32 NCHW (n, head_out, h, w).
+ * EINVAL when the layer does not fit the stacked band kernel (rows of >= 128
+ * pixels, input channels in multiples of 32, weights within shared memory).
+ */
+glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
+                                  int c1, int n, int h, int w, const void *wt,
+                                  const float *bias, int cout, void *y,
+                                  long long ys, int relu, void *pool_y,
+                                  const void *head_w, const float *head_b,
+                                  int head_out, float *head_y, int *err,
+                                  void *stream);
+
 /* Choice of tensor-core convolution kernel for glbm_nn_tc_conv (process-wide):
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
  * pixels and 32 or 64 output channels whose weights fit shared memory run the

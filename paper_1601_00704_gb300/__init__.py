@@ -38,6 +38,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_set_convergence", "glbm_batch_set_persistent", "glbm_batch_get_persistent",
            "glbm_batch_set_convergence", "glbm_nn_tc_set_variant",
            "glbm_nn_tc_conv_wgrad", "glbm_nn_tc_pack_weights_flip", "glbm_nn_bias_grad",
+           "glbm_nn_tc_conv_fused",
            "glbm_batch_create", "glbm_batch_set_medium", "glbm_batch_set_force",
            "glbm_batch_reset", "glbm_batch_set_schedule", "glbm_batch_autotune",
            "glbm_batch_step", "glbm_batch_results", "glbm_batch_get_distributions",
@@ -96,6 +97,8 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_nn_tc_conv_wgrad": ([_VP, i, i, _VP, i, i, i, i, i, i, _VP, _VP, _VP], i),
         "glbm_nn_tc_pack_weights_flip": ([_VP, i, i, i, i, i, i, _VP, _VP], i),
         "glbm_nn_bias_grad": ([_VP, ll, i, i, i, i, _VP, _VP], i),
+        "glbm_nn_tc_conv_fused": ([_VP, i, _VP, i, i, i, i, _VP, _VP, i, _VP, ll, i, _VP, _VP, _VP, i, _VP,
+                                   _VP, _VP], i),
         "glbm_batch_get_persistent": ([h, C.POINTER(i)], i),
         "glbm_load": ([h, C.c_char_p], i),
         "glbm_last_error": ([h], C.c_char_p),

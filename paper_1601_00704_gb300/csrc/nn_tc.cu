@@ -207,10 +207,19 @@ struct BandArgs {
     int c0, c1;
     int stack;  // 1: the three dy taps stacked along N (see k_tc_conv_band)
     const float *bias;
-    void *y;
+    void *y;               // BF16 NHWC output, or NULL (only the fused outputs below)
     long long ys;
     int relu;
     int *err;
+    // fused outputs (32 output channels, stacked): the 2x2 average of the
+    // BF16 output (BF16 NHWC, h/2 x w/2, cout channels), and a 1x1 head of
+    // head_out <= 4 channels (BF16 weights [head_out][32], FP32 bias) on the
+    // BF16-rounded output, written FP32 NCHW
+    __nv_bfloat16 *pool_y;
+    const __nv_bfloat16 *head_w;
+    const float *head_b;
+    float *head_y;
+    int head_out;
 };
 
 // Two groups of 32 consecutive FP32 columns of this thread's TMEM lane,
@@ -246,6 +255,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ float sbias[64];
+    __shared__ float shead[4 * 32], shead_b[4];
 
     // an all-zero A operand (128 rows x 16 K, unswizzled): MMAs with it and
     // accumulate = 0 clear the stacked accumulator slots of a band
@@ -254,6 +264,8 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = a.stages;
     if (threadIdx.x < a.cout) sbias[threadIdx.x] = a.bias[threadIdx.x];
+    if (a.head_y && threadIdx.x < a.head_out * 32) shead[threadIdx.x] = __bfloat162float(a.head_w[threadIdx.x]);
+    if (a.head_y && threadIdx.x < a.head_out) shead_b[threadIdx.x] = a.head_b[threadIdx.x];
     for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
@@ -413,28 +425,77 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 }
                 tmem_ld32x2(buf + uint32_t(rr[0] + first_slot) * a.acc_row + uint32_t(cc0[0]),
                             buf + uint32_t(rr[1] + first_slot) * a.acc_row + uint32_t(cc0[1]), v[0], v[1]);
+                // bias, ReLU, BF16 rounding (the fused outputs start from the
+                // rounded values, as the separate kernels would read them)
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (g + u >= ngroups) break;
-                    const int py = by * a.R + rr[u];
-                    if (px >= a.w || py >= a.h) continue;
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
-                                                           (((long long)img * a.h + py) * a.w + px) * a.ys + cc0[u]);
+                for (int u = 0; u < 2; ++u)
 #pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4) {
-                        uint32_t pk[4];
+                    for (int cc = 0; cc < 32; ++cc) {
+                        float x = v[u][cc] + sbias[cc0[u] + cc];
+                        if (a.relu) x = fmaxf(x, 0.0f);
+                        v[u][cc] = __bfloat162float(__float2bfloat16_rn(x));
+                    }
+                const bool colok = px < a.w;
+                if (a.y) {
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int cc = j4 * 8 + 2 * j;
-                            float lo = v[u][cc] + sbias[cc0[u] + cc], hi = v[u][cc + 1] + sbias[cc0[u] + cc + 1];
-                            if (a.relu) {
-                                lo = fmaxf(lo, 0.0f);
-                                hi = fmaxf(hi, 0.0f);
+                    for (int u = 0; u < 2; ++u) {
+                        if (g + u >= ngroups) break;
+                        const int py = by * a.R + rr[u];
+                        if (!colok || py >= a.h) continue;
+                        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
+                                                               (((long long)img * a.h + py) * a.w + px) * a.ys + cc0[u]);
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4) {
+                            uint32_t pk[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[u][j4 * 8 + 2 * j], v[u][j4 * 8 + 2 * j + 1]);
+                                pk[j] = *reinterpret_cast<uint32_t *>(&b2);
                             }
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(lo, hi);
-                            pk[j] = *reinterpret_cast<uint32_t *>(&b2);
+                            dst[j4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
-                        dst[j4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
+                if (a.head_y) {
+                    // 1x1 head on this pixel's 32 channels, per row of the pair
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (g + u >= ngroups) break;
+                        const int py = by * a.R + rr[u];
+                        for (int k = 0; k < a.head_out; ++k) {
+                            float acc_h = 0.0f;
+#pragma unroll
+                            for (int cc = 0; cc < 32; ++cc) acc_h = fmaf(v[u][cc], shead[k * 32 + cc], acc_h);
+                            if (colok && py < a.h)
+                                a.head_y[(((long long)img * a.head_out + k) * a.h + py) * a.w + px] = acc_h + shead_b[k];
+                        }
+                    }
+                }
+                if (a.pool_y) {
+                    // rows rr[0], rr[0] + 1 (even) of the pair and pixels px, px ^ 1 (lanes
+                    // lane, lane ^ 1): FP32 ((a + b) + (d + e)) / 4, rounded to BF16
+                    const int pyo = (by * a.R + rr[0]) >> 1;
+                    const bool wr = (lane & 1) == 0 && colok && pyo < (a.h >> 1);
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int cc = 0; cc < 32; cc += 2) {
+                        float s2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float mine_top = v[0][cc + e], mine_bot = v[1][cc + e];
+                            const float nb_top = __shfl_xor_sync(0xffffffffu, mine_top, 1);
+                            const float nb_bot = __shfl_xor_sync(0xffffffffu, mine_bot, 1);
+                            s2[e] = 0.25f * ((mine_top + nb_top) + (mine_bot + nb_bot));
+                        }
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(s2[0], s2[1]);
+                        pk[cc / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                    if (wr) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(
+                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * 32);
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4)
+                            dst[j4] = make_uint4(pk[4 * j4], pk[4 * j4 + 1], pk[4 * j4 + 2], pk[4 * j4 + 3]);
                     }
                 }
             }
@@ -622,7 +683,9 @@ bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int
 
 glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
                         const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
-                        int R, int stages, size_t smem, int stack) {
+                        int R, int stages, size_t smem, int stack, void *pool_y = nullptr,
+                        const void *head_w = nullptr, const float *head_b = nullptr, float *head_y = nullptr,
+                        int head_out = 0) {
     CUtensorMap mA0, mA1;
     if (!map_act_band(&mA0, x0, c0, w, h, n, R) ||
         !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, R))
@@ -648,6 +711,11 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     a.tx_bytes = uint32_t(4 * (R + 2) * BAND_PX * 16);
     a.wtile = uint32_t(cout * TC_KC * 2);
     a.stack = stack;
+    a.pool_y = static_cast<__nv_bfloat16 *>(pool_y);
+    a.head_w = static_cast<const __nv_bfloat16 *>(head_w);
+    a.head_b = head_b;
+    a.head_y = head_y;
+    a.head_out = head_out;
     a.acc_row = 32;
     while (a.acc_row < uint32_t(cout)) a.acc_row <<= 1;
     // stacked: row slots -2 .. R + 1, exactly cout columns apart
@@ -750,6 +818,41 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     kern<<<grid, TC_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(mA0, mA1, mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch");
+}
+
+extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1, int c1, int n, int h, int w,
+                                             const void *wt, const float *bias, int cout, void *y, long long ys,
+                                             int relu, void *pool_y, const void *head_w, const float *head_b,
+                                             int head_out, float *head_y, int *err, void *stream) {
+    if (!x0 || !wt || !bias || !err || (c1 > 0 && !x1) || (!y && !pool_y && !head_y))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: x0, wt, bias, err and at least one output are required");
+    if (n < 1 || h < 1 || w < 1 || c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC || cout != 32)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: needs 32 output channels and input channels in multiples of 32");
+    if (y && (ys < cout || ys % 8)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: bad output pixel stride");
+    if (pool_y && (h % 2 || w % 2)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: pooling needs even h and w");
+    if (head_y && (!head_w || !head_b || head_out < 1 || head_out > 4))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the head needs weights, bias and 1..4 outputs");
+    const uintptr_t mis = (uintptr_t(x0) | uintptr_t(x1) | uintptr_t(wt) | uintptr_t(y) | uintptr_t(pool_y)) & 15u;
+    if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: arrays must be 16-byte aligned");
+    if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: cuTensorMapEncodeTiled is not available");
+    const int cin = c0 + c1;
+    int R = 0, stages = 0, stack = 0;
+    size_t smem = 0;
+    if (!band_plan(3, 0, w, cin, cout, h, &R, &stages, &smem, &stack) || !stack || (pool_y && R % 2))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the layer does not fit the stacked band kernel");
+    CUtensorMap mB;
+    {
+        const cuuint64_t dims[3] = {cuuint64_t(cin), cuuint64_t(cout), 9};
+        const cuuint64_t strides[2] = {cuuint64_t(cin) * 2, cuuint64_t(cin) * 2 * cout};
+        const cuuint32_t box[3] = {TC_KC, cuuint32_t(cout), 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (encode_fn()(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wt), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: weight tensor map rejected");
+    }
+    return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
+                       R, stages, smem, stack, pool_y, head_w, head_b, head_y, head_out);
 }
 
 extern "C" glbm_status glbm_nn_tc_pack_weights(const float *wf, int cout, int cin, int k, int cout_pad,

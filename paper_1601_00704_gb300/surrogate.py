@@ -458,10 +458,13 @@ class UNet:
             C.c_void_p(y.data_ptr()), cop, int(relu), int(head), self.out_ch if head else 0,
             C.c_void_p(B["err"].data_ptr()), self._stream()), "tc_conv")
 
-    def forward_tc(self, x):
+    def forward_tc(self, x, fused=True):
         """The forward pass on the tensor cores: x (n, in_ch, h, w) FP32 CUDA
         tensor -> (n, out_ch, h, w) FP32.  Activations are BF16 NHWC between
-        layers, accumulation FP32; the pipeline's error flag is checked."""
+        layers, accumulation FP32; the pipeline's error flag is checked.
+        fused: where the first level has 32 channels and rows of >= 128
+        pixels, its 2x2 pooling and the 1x1 head run inside the epilogues of
+        the convolutions before them (glbm_nn_tc_conv_fused)."""
         n, _, h, w = x.shape
         self._tc_pack()
         B = self._tc_buffers(n, h, w)
@@ -471,13 +474,18 @@ class UNet:
                                                cin, st), "nchw_to_nhwc")
         L = self.levels
         inp = B["x"]
+        fuse0 = fused and self.ch[0] == 32 and w >= 128
         for l in range(L):
             hl, wl, c = h >> l, w >> l, self.ch[l]
             self._tc_conv(B, inp, cin, None, 0, n, hl, wl, f"e{l}a", True, B[f"a{l}"])
-            self._tc_conv(B, B[f"a{l}"], c, None, 0, n, hl, wl, f"e{l}b", True, B[f"e{l}"])
+            if l == 0 and fuse0 and L > 1:
+                self._tc_fused(B, B["a0"], c, n, hl, wl, "e0b", y=B["e0"], pool_y=B["p0"])
+            else:
+                self._tc_conv(B, B[f"a{l}"], c, None, 0, n, hl, wl, f"e{l}b", True, B[f"e{l}"])
+                if l < L - 1:
+                    self._ok(self.lib.glbm_nn_pool2_nhwc(C.c_void_p(B[f"e{l}"].data_ptr()), n, c, hl, wl,
+                                                         C.c_void_p(B[f"p{l}"].data_ptr()), st), "pool2_nhwc")
             if l < L - 1:
-                self._ok(self.lib.glbm_nn_pool2_nhwc(C.c_void_p(B[f"e{l}"].data_ptr()), n, c, hl, wl,
-                                                     C.c_void_p(B[f"p{l}"].data_ptr()), st), "pool2_nhwc")
                 inp, cin = B[f"p{l}"], c
         top, ctop = B[f"e{L - 1}"], self.ch[L - 1]
         for l in range(L - 2, -1, -1):
@@ -485,10 +493,22 @@ class UNet:
             self._ok(self.lib.glbm_nn_upsample2_nhwc(C.c_void_p(top.data_ptr()), n, ctop, hl // 2, wl // 2,
                                                      C.c_void_p(B[f"u{l}"].data_ptr()), st), "upsample2_nhwc")
             self._tc_conv(B, B[f"u{l}"], ctop, B[f"e{l}"], c, n, hl, wl, f"d{l}a", True, B[f"da{l}"])
+            if l == 0 and fuse0:
+                # d0b with the 1x1 head in its epilogue: d0 itself is never stored
+                self._tc_fused(B, B["da0"], c, n, hl, wl, "d0b", head=True)
+                return B["y"]
             self._tc_conv(B, B[f"da{l}"], c, None, 0, n, hl, wl, f"d{l}b", True, B[f"d{l}"])
             top, ctop = B[f"d{l}"], c
         self._tc_conv(B, top, ctop, None, 0, n, h, w, "head", False, B["y"], head=True)
         return B["y"]
+
+    def _tc_fused(self, B, x0, c0, n, h, w, name, y=None, pool_y=None, head=False):
+        _, W, Bs = self._tc
+        vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._ok(self.lib.glbm_nn_tc_conv_fused(
+            vp(x0), c0, None, 0, n, h, w, vp(W[name]), vp(Bs[name]), 32, vp(y), 32, 1, vp(pool_y),
+            vp(W["head"]) if head else None, vp(Bs["head"]) if head else None, self.out_ch if head else 0,
+            vp(B["y"]) if head else None, vp(B["err"]), self._stream()), "tc_conv_fused")
 
     def tc_error(self):
         """Nonzero if a tensor-core pipeline wait timed out since the buffers

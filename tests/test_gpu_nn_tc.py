@@ -170,6 +170,28 @@ def test_unet_forward_tc_matches_fp32(pkg, levels, max_ch, size):
     assert rel < 2e-2, rel
 
 
+@pytest.mark.parametrize("levels,size", [(3, 256), (6, 512)])
+def test_unet_forward_tc_fused_matches_unfused(pkg, levels, size):
+    """The fused first level (2x2 pool and 1x1 head inside the band kernel's
+    epilogues) gives what the separate kernels give: the pooled tensor
+    exactly (same arithmetic on the same BF16 values), the network output
+    to FP32 summation order."""
+    import torch
+    from paper_1601_00704_gb300.surrogate import UNet
+    net = UNet(base=32, levels=levels, seed=7, max_ch=128)
+    rng = np.random.default_rng(17)
+    x = torch.from_numpy(rng.normal(size=(2, 3, size, size)).astype(np.float32)).cuda()
+    y0 = net.forward_tc(x, fused=False).clone()
+    p0 = net._tc_bufs[(2, size, size)]["p0"].clone()
+    y1 = net.forward_tc(x, fused=True).clone()
+    p1 = net._tc_bufs[(2, size, size)]["p0"].clone()
+    torch.cuda.synchronize()
+    assert net.tc_error() == 0
+    assert torch.equal(p0, p1)
+    rel = float((y1 - y0).abs().max() / y0.abs().max())
+    assert rel < 1e-5, rel
+
+
 def test_trained_network_tc_prediction(pkg):
     """The committed network on an unseen medium of its training recipe: the
     tensor-core prediction matches the FP32 one in every output channel."""
