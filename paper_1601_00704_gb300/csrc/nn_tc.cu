@@ -186,11 +186,11 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
 // row, horizontal tap and 16 channels feeds three output rows' accumulator
 // slots at once (each band first clears its slots with MMAs of an all-zero
 // A operand and accumulate = 0).
-// Roles: warp 0 issues TMA, warp 3 the MMAs, warps 4-11 run the epilogue,
-// two per TMEM lane quarter (a warp reads the lanes of its index mod 4), each
-// taking alternate row pairs (warps 1-2 idle); every wait is bounded.
+// Roles: warp 0 issues TMA, warp 3 the MMAs, warps 4-7 run the epilogue
+// (warps 1-2 idle: the TMEM lane quarters fix the epilogue to warps whose
+// index is 0-3 mod 4); every wait is bounded.
 constexpr int BAND_PX = TC_M + 2;   // halo pixels per row
-constexpr int BAND_THREADS = 384;
+constexpr int BAND_THREADS = 256;
 
 struct BandArgs {
     int n, h, w, nchunk0, nchunk, cout, R, stages;
@@ -276,7 +276,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
         mbar_init(&wfull, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
-            mbar_init(&accempty[b], 8);  // one arrival per epilogue warp
+            mbar_init(&accempty[b], 4);  // one arrival per epilogue warp
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -414,10 +414,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             const uint32_t buf = tmem + uint32_t(ab) * a.acc_cols + lanes;
             const int first_slot = a.stack ? 2 : 0;
             const int ngroups = a.R * (a.cout / 32);
-            // two warps per TMEM lane quarter: warps 4-7 take group pairs 0, 2, ..
-            // and warps 8-11 pairs 1, 3, .. (a pair = two rows of 32 channels, or
-            // one row of 64)
-            for (int g = 2 * ((warp - 4) >> 2); g < ngroups; g += 4) {
+            for (int g = 0; g < ngroups; g += 2) {
                 float v[2][32];
                 int rr[2], cc0[2];
 #pragma unroll
