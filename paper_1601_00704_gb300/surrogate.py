@@ -510,6 +510,16 @@ class UNet:
             vp(W["head"]) if head else None, vp(Bs["head"]) if head else None, self.out_ch if head else 0,
             vp(B["y"]) if head else None, vp(B["err"]), self._stream()), "tc_conv_fused")
 
+    def flops(self, h, w, n=1):
+        """Multiply-add work of one forward pass, 2 * pixels * cin * cout * k^2
+        summed over the convolutions (real channel counts, no padding)."""
+        level = {}
+        for l in range(self.levels):
+            level[f"e{l}a"] = level[f"e{l}b"] = l
+            level[f"d{l}a"] = level[f"d{l}b"] = l
+        level["head"] = 0
+        return sum(2.0 * n * (h >> level[nm]) * (w >> level[nm]) * ci * co * k * k for nm, ci, co, k in self.specs)
+
     def tc_error(self):
         """Nonzero if a tensor-core pipeline wait timed out since the buffers
         were made, in inference or training (synchronises)."""

@@ -356,11 +356,24 @@ def infer_timing(net, n, seed=4242, reps=3, tc=True):
         surrogate.predict_device(net, eps_d, K_d, G, NU, tc=tc)
     e1.record()
     e1.synchronize()
+    pred_ms = e0.elapsed_time(e1) / reps
+    # the network alone, on the features of the same medium
+    x = torch.from_numpy(surrogate.features(m["eps"], K, G)[None]).cuda()
+    fwd = (lambda: net.forward_tc(x)) if tc else (lambda: net.forward(x))
+    fwd()
+    e0.record()
+    for _ in range(reps):
+        fwd()
+    e1.record()
+    e1.synchronize()
+    net_ms = e0.elapsed_time(e1) / reps
     err = net.tc_error() if tc else 0
     if err:
         raise RuntimeError(f"tensor-core pipeline reported a timeout (code {err})")
+    fl = net.flops(n, n)
     return {"n": n, "path": "tensor cores (tcgen05, BF16)" if tc else "FP32 kernels",
-            "ms_per_prediction": e0.elapsed_time(e1) / reps}
+            "ms_per_prediction": pred_ms, "network_ms": net_ms, "network_tflop": fl / 1e12,
+            "network_pflops": fl / (net_ms * 1e-3) / 1e15}
 
 
 def _study_one(net, n, seed, ref_tol, check):
