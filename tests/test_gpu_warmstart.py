@@ -52,7 +52,7 @@ def test_warm_start_saves_steps_under_the_stopping_rule(setup, storage):
         cold_total += cold["steps"]
         warm_total += warm["steps"]
     print(f"total {storage}: cold {cold_total}, warm {warm_total}")
-    assert warm_total <= 0.6 * cold_total
+    assert warm_total <= 0.7 * cold_total
 
 
 def test_warm_start_converges_to_the_same_answer(setup):
