@@ -488,19 +488,21 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
                             int cout_store, int *err, void *stream);
 
 /*
- * The band kernel of a 3x3 convolution with 32 output channels (as in
+ * The band kernel of a 3x3 convolution with 32 or 64 output channels (as in
  * glbm_nn_tc_conv, bias and ReLU applied) with outputs fused into its
  * epilogue, so that the layers that follow need no pass of their own:
  *   y       BF16 NHWC output (pixel stride ys), or NULL when only the fused
  *           outputs are wanted;
  *   pool_y  if not NULL, the 2x2 average of the BF16 output, BF16 NHWC
- *           (n, h/2, w/2, 32), computed as glbm_nn_pool2_nhwc does (h, w
+ *           (n, h/2, w/2, cout), computed as glbm_nn_pool2_nhwc does (h, w
  *           even);
- *   head_y  if not NULL, a 1x1 convolution (the network's head) of the BF16
- *           output: head_w BF16 [head_out][32], head_b FP32 [head_out],
- *           head_out in 1..4, written FP32 NCHW (n, head_out, h, w).
- * EINVAL when the layer does not fit the stacked band kernel (rows of >= 128
- * pixels, input channels in multiples of 32, weights within shared memory).
+ *   head_y  if not NULL (32 output channels only), a 1x1 convolution (the
+ *           network's head) of the BF16 output: head_w BF16 [head_out][32],
+ *           head_b FP32 [head_out], head_out in 1..4, written FP32 NCHW
+ *           (n, head_out, h, w).
+ * EINVAL when the layer does not fit the band kernel (rows of >= 128 pixels,
+ * input channels in multiples of 32, weights within shared memory; with 32
+ * output channels the stacked form).
  */
 glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
                                   int c1, int n, int h, int w, const void *wt,
@@ -510,15 +512,22 @@ glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
                                   int head_out, float *head_y, int *err,
                                   void *stream);
 
-/* Choice of tensor-core convolution kernel for glbm_nn_tc_conv (process-wide):
+/* Choice of tensor-core convolution kernel for glbm_nn_tc_conv and
+ * glbm_nn_tc_conv_fused (process-wide):
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
  * pixels and 32 or 64 output channels whose weights fit shared memory run the
  * band kernel (weights resident, each band's halo loaded once per 32-channel
  * chunk; with 32 output channels the three vertical taps are stacked into
- * one MMA of 96 columns); the rest run the tile kernel (one 128-pixel tile
- * per CTA, one TMA tile per tap); 1 = tile kernel always; 2 = as 0; 3 = band
- * kernel where it applies but never stacked.  All compute the same
- * convolution; other values reset to 0. */
+ * one MMA of 96 columns), and those with 32 output channels where one CTA
+ * per (image, 128-pixel strip) leaves segments of >= 16 rows per SM run its
+ * streaming form (each CTA walks down its strip, each input row multiplied
+ * once into a ring of row accumulators); the rest run the tile kernel (one
+ * 128-pixel tile per CTA, one TMA tile per tap; a 3-stage TMA ring, or an
+ * 8-stage one when the grid has at most one CTA per SM); 1 = tile kernel
+ * always; 2 = as 0 but the tile kernel always with the 3-stage ring; 3 =
+ * band kernel where it applies but never stacked or streaming; 4 = band
+ * kernel, stacked, never streaming; 5 = as 0 with streaming however short
+ * its segments.  All compute the same convolution; other values reset to 0. */
 void glbm_nn_tc_set_variant(int variant);
 
 /* FP32 [cout][cin][ksize][ksize] -> BF16 [ksize^2][cout_pad][cin_pad] (the
@@ -559,6 +568,16 @@ glbm_status glbm_nn_bias_grad(const float *dy, long long dybs, int c, int n,
 /* FP32 NCHW (n, c, h, w) -> BF16 NHWC with c_pad >= c channels (zero);
  * c_pad a multiple of 8, y 16-byte aligned. */
 glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h, int w,
+                                 void *y, int c_pad, void *stream);
+
+/* 3x3 patches of FP32 NCHW (n, c, h, w) as BF16 NHWC channels: channel
+ * ci * 9 + 3 (dy + 1) + (dx + 1) of output pixel (y, x) is x[ci][y + dy]
+ * [x + dx] (zero outside the image), channels 9c .. c_pad - 1 are zero.
+ * A 3x3 convolution with zero padding of x then equals the 1x1 convolution
+ * (glbm_nn_tc_conv with ksize 1) of this tensor with the FP32 weights
+ * [cout][c][3][3] read as [cout][9c][1][1].  c_pad >= 9c, a multiple of 8;
+ * y 16-byte aligned. */
+glbm_status glbm_nn_im2col3_nhwc(const float *x, int n, int c, int h, int w,
                                  void *y, int c_pad, void *stream);
 
 /* 2x2 average pool, BF16 NHWC (n, h, w, c) -> (n, h/2, w/2, c); c, h, w even. */

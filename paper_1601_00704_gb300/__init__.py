@@ -48,7 +48,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_nn_conv_fwd", "glbm_nn_conv_bwd_data", "glbm_nn_conv_bwd_weight",
            "glbm_nn_relu_bwd", "glbm_nn_copy_channels", "glbm_nn_pool2",
            "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam", "glbm_em_gmm1d",
-           "glbm_nn_tc_conv", "glbm_nn_tc_pack_weights", "glbm_nn_nchw_to_nhwc",
+           "glbm_nn_tc_conv", "glbm_nn_tc_pack_weights", "glbm_nn_nchw_to_nhwc", "glbm_nn_im2col3_nhwc",
            "glbm_nn_pool2_nhwc", "glbm_nn_upsample2_nhwc", "glbm_nn_warm_features",
            "glbm_nn_warm_decode"]
 
@@ -133,6 +133,7 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_nn_tc_conv": ([_VP, i, _VP, i, i, i, i, i, _VP, _VP, i, _VP, ll, i, i, i, _VP, _VP], i),
         "glbm_nn_tc_pack_weights": ([_VP, i, i, i, i, i, _VP, _VP], i),
         "glbm_nn_nchw_to_nhwc": ([_VP, i, i, i, i, _VP, i, _VP], i),
+        "glbm_nn_im2col3_nhwc": ([_VP, i, i, i, i, _VP, i, _VP], i),
         "glbm_nn_pool2_nhwc": ([_VP, i, i, i, i, _VP, _VP], i),
         "glbm_nn_upsample2_nhwc": ([_VP, i, i, i, i, _VP, _VP], i),
         "glbm_nn_warm_features": ([_VP, _VP, ll, d, _VP, _VP], i),

@@ -17,7 +17,8 @@
 //    c1 of x1): the decoder's skip concatenation is never materialised;
 //  * one CTA per output tile (two tiles stacked in y, sharing every weight
 //    slice, when cout <= 64) with a 3-stage TMA ring (short, so that 4-6
-//    CTAs share an SM and hide each other's latency): warp 0 issues TMA,
+//    CTAs share an SM and hide each other's latency; a grid that leaves
+//    SMs empty takes a deeper ring instead): warp 0 issues TMA,
 //    warp 1 issues tcgen05.mma
 //    into a TMEM accumulator, warps 2-5 read it back (tcgen05.ld), add the
 //    bias, apply ReLU and store BF16 NHWC (or FP32 NCHW for the head);
@@ -41,7 +42,8 @@ struct TcConvArgs {
 
 // MT output tiles per CTA, stacked in y (tile t covers rows y0 + t th ..):
 // they share every weight slice and accumulate into MT TMEM accumulators.
-template <int MT>
+// S: depth of the TMA ring.
+template <int MT, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
           const __grid_constant__ CUtensorMap mapB, const TcConvArgs a) {
@@ -49,7 +51,6 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int stage_b = a.cout * TC_KC * 2;
     uint8_t *sA = smem;
-    constexpr int S = TC_STAGES;
     uint8_t *sB = smem + S * MT * TC_STAGE_A;
     __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_base;
@@ -211,10 +212,10 @@ struct BandArgs {
     long long ys;
     int relu;
     int *err;
-    // fused outputs (32 output channels, stacked): the 2x2 average of the
-    // BF16 output (BF16 NHWC, h/2 x w/2, cout channels), and a 1x1 head of
-    // head_out <= 4 channels (BF16 weights [head_out][32], FP32 bias) on the
-    // BF16-rounded output, written FP32 NCHW
+    // fused outputs: the 2x2 average of the BF16 output (BF16 NHWC, h/2 x
+    // w/2, cout channels; 32 or 64 output channels), and (32 output
+    // channels, stacked) a 1x1 head of head_out <= 4 channels (BF16 weights
+    // [head_out][32], FP32 bias) on the BF16-rounded output, written FP32 NCHW
     __nv_bfloat16 *pool_y;
     const __nv_bfloat16 *head_w;
     const float *head_b;
@@ -409,19 +410,26 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             const int by = int(rest % a.nby), img = int(rest / a.nby);
             const int px = bx * TC_M + q * 32 + lane;
             // two 32-column groups per TMEM wait: two rows of 32 channels, or
-            // one row of 64
+            // one row of 64; with pooling always the same 32 channels of two
+            // rows 2k, 2k + 1 (R is even)
             const uint32_t lanes = uint32_t(q * 32) << 16;
             const uint32_t buf = tmem + uint32_t(ab) * a.acc_cols + lanes;
             const int first_slot = a.stack ? 2 : 0;
-            const int ngroups = a.R * (a.cout / 32);
+            const int ncg = a.cout / 32;
+            const int ngroups = a.R * ncg;
             for (int g = 0; g < ngroups; g += 2) {
                 float v[2][32];
                 int rr[2], cc0[2];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const int gg = g + u < ngroups ? g + u : g;  // an odd last group loads twice
-                    rr[u] = gg / (a.cout / 32);
-                    cc0[u] = (gg % (a.cout / 32)) * 32;
+                    if (a.pool_y) {
+                        rr[u] = (g / 2 / ncg) * 2 + u;
+                        cc0[u] = (g / 2 % ncg) * 32;
+                    } else {
+                        const int gg = g + u < ngroups ? g + u : g;  // an odd last group loads twice
+                        rr[u] = gg / ncg;
+                        cc0[u] = (gg % ncg) * 32;
+                    }
                 }
                 tmem_ld32x2(buf + uint32_t(rr[0] + first_slot) * a.acc_row + uint32_t(cc0[0]),
                             buf + uint32_t(rr[1] + first_slot) * a.acc_row + uint32_t(cc0[1]), v[0], v[1]);
@@ -492,7 +500,8 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                     }
                     if (wr) {
                         uint4 *dst = reinterpret_cast<uint4 *>(
-                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * 32);
+                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * a.cout +
+                            cc0[0]);
 #pragma unroll
                         for (int j4 = 0; j4 < 4; ++j4)
                             dst[j4] = make_uint4(pk[4 * j4], pk[4 * j4 + 1], pk[4 * j4 + 2], pk[4 * j4 + 3]);
@@ -509,6 +518,321 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     if (warp == 3) {
         tc_fence_after();
         tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+// ---- Streaming variant for 32 output channels --------------------------------
+// The band kernel above clears and drains its accumulator per band of R = 4
+// rows: the stacked MMA of each of the band's R + 2 halo rows also feeds the
+// two rows above and below the band, 1.5x the MMAs the outputs need, and the
+// MMA and epilogue warps hand each band's two TMEM buffers back and forth.
+// Here each CTA owns one 128-pixel strip of one image and a segment of L
+// output rows and walks down it input row by input row.  TMEM holds a ring
+// of 16 row slots of 32 columns: input row r adds, in one MMA of N = 96 per
+// horizontal tap and 16 channels, to the slots of output rows r - 1, r and
+// r + 1 (B stacks the weights of dy = +1, 0, -1), so every input row is
+// multiplied once; output row r - 1 is then complete.  Rows are handed to the
+// epilogue in pairs (8 pair slots in flight), so the MMA warp runs several
+// row pairs ahead of the epilogue.  Where the three slots of a row wrap the
+// ring (slots 14, 15, 0 or 15, 0, 1) the row takes two MMAs of the same
+// shape (an MMA of another N in between stalls the tensor pipe): one on
+// slots 13-15 and one on slots 0-2, their B windows shifted over zero tiles
+// so that each adds only its part.  The weights of one (chunk, dx) sit as
+// [0 0 W(+1) W(0) W(-1) 0 0] in shared memory, neighbours sharing their
+// zero tiles.
+// Roles: warp 0 TMA (G input rows of one 32-channel chunk per stage: boxes
+// of G rows, as tall as the band kernel's, keep the TMA engine streaming),
+// warp 1 MMA and TMEM, warps 4-7 epilogue (one per lane quarter); every wait
+// is bounded.
+constexpr int ST_THREADS = 256;
+constexpr int ST_SLOTS = 16;
+constexpr int ST_PAIRS = ST_SLOTS / 2;
+constexpr int ST_SMAX = 12;
+
+struct StreamArgs {
+    int n, h, w, nchunk0, nchunk, nbx, nseg, L, stages;
+    uint32_t blk_stride;   // bytes between the 8-channel blocks of a stage (LBO)
+    uint32_t stage_bytes;  // 4 blocks
+    uint32_t tx_bytes;     // bytes the 4 TMA loads of a stage deliver
+    uint32_t wtile;        // bytes of one weight slice (32 rows x 64 B)
+    const float *bias;
+    void *y;  // BF16 NHWC output, or NULL (only the fused outputs)
+    long long ys;
+    int relu;
+    int *err;
+    __nv_bfloat16 *pool_y;  // as in BandArgs
+    const __nv_bfloat16 *head_w;
+    const float *head_b;
+    float *head_y;
+    int head_out;
+};
+
+template <int G>
+__global__ void __launch_bounds__(ST_THREADS, 1)
+k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
+                 const __grid_constant__ CUtensorMap mapB, const StreamArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int ntile_w = 9 * a.nchunk;
+    const int nslot_w = 15 * a.nchunk + 2;  // weight tiles with their zero tiles
+    uint8_t *sW = smem;
+    uint8_t *sA = smem + size_t(nslot_w) * a.wtile;
+    __shared__ __align__(8) uint64_t full[ST_SMAX], empty[ST_SMAX], wfull, pfull[ST_PAIRS], pempty[ST_PAIRS];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+    __shared__ __align__(16) float sbias[32];
+    __shared__ float shead[4 * 32], shead_b[4];
+    __shared__ __align__(128) uint8_t szero[4096];  // all-zero A (128 rows x 16 K, unswizzled)
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = a.stages;
+    const int seg = int(blockIdx.x % unsigned(a.nseg));
+    const int rest = int(blockIdx.x / unsigned(a.nseg));
+    const int bx = rest % a.nbx, img = rest / a.nbx;
+    const int ya = seg * a.L;
+    const int Lseg = min(a.L, a.h - ya);
+    // input rows ya - 1 .. ya + Lseg (local index ir = 0 .. Lseg + 1), G per
+    // group; output row j (row ya - 2 + j, slot j mod 16) takes input rows
+    // j - 2 .. j, so row pair P (j = 2P, 2P + 1) is complete after the group
+    // holding input row 2P + 1; pair 0 (rows above the segment) is never
+    // stored, pairs 1 .. npairs are
+    constexpr int hg = G / 2;
+    const int ngroups = (Lseg + 2 + G - 1) / G;
+    const int npairs = (Lseg + 1) / 2;
+    if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias[threadIdx.x];
+    if (a.head_y && threadIdx.x < a.head_out * 32) shead[threadIdx.x] = __bfloat162float(a.head_w[threadIdx.x]);
+    if (a.head_y && threadIdx.x < a.head_out) shead_b[threadIdx.x] = a.head_b[threadIdx.x];
+    for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
+    {
+        // the zero tiles: 0, 1 and 5 + 5k, 6 + 5k around (chunk, dx) group k
+        const int per = int(a.wtile / 16);
+        for (int j = threadIdx.x; j < nslot_w * per; j += blockDim.x) {
+            const int t = j / per;
+            if (t < 2 || (t - 2) % 5 >= 3) reinterpret_cast<uint4 *>(sW)[j] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&wfull, 1);
+        for (int p = 0; p < ST_PAIRS; ++p) {
+            mbar_init(&pfull[p], 1);
+            mbar_init(&pempty[p], 4);  // the four lane-quarter epilogue warps
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const int x0 = bx * TC_M;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
+            for (int tap = 0; tap < 9; ++tap)
+                for (int ch = 0; ch < a.nchunk; ++ch)
+                    tma_load_3d(sW + size_t(2 + 5 * (ch * 3 + tap % 3) + (2 - tap / 3)) * a.wtile, &mapB, &wfull,
+                                ch * TC_KC, 0, tap);
+            long long i = 0;
+            bool go = true;
+            for (int g = 0; g < ngroups && go; ++g)
+                for (int ch = 0; ch < a.nchunk; ++ch, ++i) {
+                    const int s = int(i % S);
+                    const long long use = i / S;
+                    if (use > 0 && !mbar_wait_idle(&empty[s], uint32_t(use - 1) & 1u, &abort_flag, a.err, 21)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], a.tx_bytes);
+                    uint8_t *dst = sA + size_t(s) * a.stage_bytes;
+                    const bool first = ch < a.nchunk0;
+                    const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
+#pragma unroll
+                    for (int blk = 0; blk < 4; ++blk)
+                        tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
+                                    x0 - 1, ya - 1 + G * g, img);
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id64 = idesc_bf16(64), id96 = idesc_bf16(96);
+            bool ok = mbar_wait(&wfull, 0, &abort_flag, a.err, 22);
+            tc_fence_after();
+            const uint64_t zdesc = sdesc_nosw(smem_u32(szero), 2048u, 128u);
+            const uint64_t wdesc = sdesc_k64(sW);
+            const uint32_t wt16 = a.wtile >> 4, kstep = (2 * a.blk_stride) >> 4;
+            const uint32_t d13 = uint32_t((ST_SLOTS - 3) * 32);
+            long long i = 0;
+            for (int g = 0; g < ngroups && ok; ++g) {
+                // pairs hg g + 1 .. hg g + hg enter their slots: wait until the
+                // epilogue has drained each one's last stored occupant, then
+                // clear them
+                for (int pn = hg * g + 1; pn <= hg * g + hg && ok; ++pn) {
+                    const int ps = pn % ST_PAIRS, prev = pn - ST_PAIRS;
+                    if (prev >= 1 && prev <= npairs &&
+                        !mbar_wait(&pempty[ps], uint32_t((prev - 1) / ST_PAIRS) & 1u, &abort_flag, a.err, 23)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, wdesc, id64, 0u);
+                }
+                for (int ch = 0; ch < a.nchunk && ok; ++ch, ++i) {
+                    const int s = int(i % S);
+                    if (!mbar_wait(&full[s], uint32_t(i / S) & 1u, &abort_flag, a.err, 24)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t a0 = sdesc_nosw(smem_u32(sA + size_t(s) * a.stage_bytes), a.blk_stride, 128u);
+                    // B of (chunk, dx) group k starts at tile 2 + 5k: [W(+1) W(0) W(-1)]
+                    const uint64_t b0 = sdesc_k64(sW) + uint64_t((2 + 15 * ch) * wt16);
+#pragma unroll 1
+                    for (int ri = 0; ri < G; ++ri) {
+                        // input row G g + ri feeds the slots of rows G g + ri .. + 2
+                        const int s0 = (G * g + ri) % ST_SLOTS;
+                        const uint64_t arow = a0 + uint64_t(ri * BAND_PX);  // 16-byte units
+                        if (s0 <= ST_SLOTS - 3) {
+                            const uint32_t d0 = tmem + uint32_t(s0 * 32);
+#pragma unroll
+                            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk)
+                                    umma_bf16(d0, arow + uint64_t(dxi + kk * kstep),
+                                              b0 + uint64_t(5 * dxi * wt16 + kk * 2), id96, 1u);
+                        } else {
+                            // slots 13-15 take B shifted by 1 (s0 = 14: [0 W(+1) W(0)]) or
+                            // 2 (s0 = 15: [0 0 W(+1)]) tiles; slots 0-2 the rest, shifted
+                            // the other way ([W(-1) 0 0] or [W(0) W(-1) 0])
+                            const uint32_t sh = uint32_t(s0 - (ST_SLOTS - 3));  // 1 or 2
+#pragma unroll
+                            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk) {
+                                    const uint64_t ad = arow + uint64_t(dxi + kk * kstep);
+                                    const uint64_t bk = b0 + uint64_t(5 * dxi * wt16 + kk * 2);
+                                    umma_bf16(tmem + d13, ad, bk - uint64_t(sh * wt16), id96, 1u);
+                                    umma_bf16(tmem, ad, bk + uint64_t((3 - sh) * wt16), id96, 1u);
+                                }
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                for (int pc = hg * g; pc < hg * g + hg && ok; ++pc)
+                    if (pc >= 1 && pc <= npairs) umma_commit(&pfull[pc % ST_PAIRS]);
+            }
+        }
+    } else if (warp >= 4) {
+        const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
+        const int px = x0 + q * 32 + lane;
+        const bool colok = px < a.w;
+        const uint32_t lanes = uint32_t(q * 32) << 16;
+        const float4 *sb4 = reinterpret_cast<const float4 *>(sbias);
+        for (int P = 1; P <= npairs; ++P) {
+            const int ps = P % ST_PAIRS;
+            if (!mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / ST_PAIRS) & 1u, &abort_flag, a.err, 25)) break;
+            tc_fence_after();
+            float v[2][32];
+            tmem_ld32x2(tmem + lanes + uint32_t(2 * ps * 32), tmem + lanes + uint32_t((2 * ps + 1) * 32), v[0], v[1]);
+            uint32_t pk[2][16];
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+                const float4 b4 = sb4[j4];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float x0v = v[u][4 * j4] + b4.x, x1v = v[u][4 * j4 + 1] + b4.y;
+                    float x2v = v[u][4 * j4 + 2] + b4.z, x3v = v[u][4 * j4 + 3] + b4.w;
+                    if (a.relu) {
+                        x0v = fmaxf(x0v, 0.0f);
+                        x1v = fmaxf(x1v, 0.0f);
+                        x2v = fmaxf(x2v, 0.0f);
+                        x3v = fmaxf(x3v, 0.0f);
+                    }
+                    __nv_bfloat162 b0 = __floats2bfloat162_rn(x0v, x1v), b1 = __floats2bfloat162_rn(x2v, x3v);
+                    pk[u][2 * j4] = *reinterpret_cast<uint32_t *>(&b0);
+                    pk[u][2 * j4 + 1] = *reinterpret_cast<uint32_t *>(&b1);
+                }
+            }
+            const int r0 = 2 * P - 2;  // segment row of the pair's first row
+            if (a.y && colok) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (r0 + u >= Lseg) break;
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
+                                                           (((long long)img * a.h + ya + r0 + u) * a.w + px) * a.ys);
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4)
+                        dst[j4] = make_uint4(pk[u][4 * j4], pk[u][4 * j4 + 1], pk[u][4 * j4 + 2], pk[u][4 * j4 + 3]);
+                }
+            }
+            if (a.pool_y || a.head_y) {
+                // the fused outputs start from the BF16-rounded values
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pk[u][j]));
+                        v[u][2 * j] = f.x;
+                        v[u][2 * j + 1] = f.y;
+                    }
+            }
+            if (a.head_y) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (r0 + u >= Lseg) break;
+                    for (int k = 0; k < a.head_out; ++k) {
+                        float acc_h = 0.0f;
+#pragma unroll
+                        for (int cc = 0; cc < 32; ++cc) acc_h = fmaf(v[u][cc], shead[k * 32 + cc], acc_h);
+                        if (colok)
+                            a.head_y[(((long long)img * a.head_out + k) * a.h + ya + r0 + u) * a.w + px] =
+                                acc_h + shead_b[k];
+                    }
+                }
+            }
+            if (a.pool_y) {
+                // rows r0, r0 + 1 (ya and r0 even) and pixels px, px ^ 1 (lanes
+                // lane, lane ^ 1): FP32 ((a + b) + (d + e)) / 4, rounded to BF16
+                const bool wr = (lane & 1) == 0 && colok && r0 + 1 < Lseg;
+                uint32_t pp[16];
+#pragma unroll
+                for (int cc = 0; cc < 32; cc += 2) {
+                    float s2[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float mine_top = v[0][cc + e], mine_bot = v[1][cc + e];
+                        const float nb_top = __shfl_xor_sync(0xffffffffu, mine_top, 1);
+                        const float nb_bot = __shfl_xor_sync(0xffffffffu, mine_bot, 1);
+                        s2[e] = 0.25f * ((mine_top + nb_top) + (mine_bot + nb_bot));
+                    }
+                    __nv_bfloat162 b2 = __floats2bfloat162_rn(s2[0], s2[1]);
+                    pp[cc / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                }
+                if (wr) {
+                    const int pyo = (ya + r0) >> 1;
+                    uint4 *dst = reinterpret_cast<uint4 *>(
+                        a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * 32);
+#pragma unroll
+                    for (int j4 = 0; j4 < 4; ++j4)
+                        dst[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&pempty[ps])) : "memory");
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -530,6 +854,39 @@ __global__ void k_nchw_to_nhwc(const float *__restrict__ x, int n, int c, int h,
                 const float vb = b < c ? x[(img * c + b) * hw + p] : 0.0f;
                 __nv_bfloat162 t = __floats2bfloat162_rn(va, vb);
                 pk[j] = *reinterpret_cast<uint32_t *>(&t);
+            }
+            y[pix * (cp / 8) + c0 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+}
+
+// 3x3 patches (zero outside the image) as channels: y[pixel][ci * 9 + t] =
+// x[ci][py + dy][px + dx] with t = 3 (dy + 1) + (dx + 1), the same order as
+// the FP32 weights [cout][cin][3][3] flattened, so a 3x3 convolution of x is
+// the 1x1 convolution of y with those weights read as [cout][9 cin]; the
+// channels from 9c up to cp are zero.  One thread per output pixel.
+__global__ void k_im2col3_nhwc(const float *__restrict__ x, int n, int c, int h, int w, uint4 *__restrict__ y,
+                               int cp) {
+    const long long hw = (long long)h * w, total = (long long)n * hw;
+    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < total;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const long long img = pix / hw, p = pix - img * hw;
+        const int py = int(p / w), px = int(p - (long long)py * w);
+        for (int c0 = 0; c0 < cp; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = c0 + j, ci = k / 9, t = k - 9 * ci;
+                const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+                v[j] = (ci < c && yy >= 0 && yy < h && xx >= 0 && xx < w)
+                           ? x[(img * c + ci) * hw + (long long)yy * w + xx]
+                           : 0.0f;
+            }
+            uint32_t pk[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                __nv_bfloat162 t2 = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                pk[j] = *reinterpret_cast<uint32_t *>(&t2);
             }
             y[pix * (cp / 8) + c0 / 8] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
@@ -641,8 +998,10 @@ bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, i
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 0 = choose per layer, 1 = tile kernel only, 2 = band kernel where it
-// applies (glbm_nn_tc_set_variant).
+// 0 = choose per layer, 1 = tile kernel only, 2 = as 0 with the tile
+// kernel's ring never deepened, 3 = band kernel never stacked, 4 = band
+// kernel stacked but never streaming, 5 = streaming wherever it applies,
+// however short its segments (glbm_nn_tc_set_variant).
 int g_tc_variant = 0;
 // dynamic shared memory budget: the 227 KB opt-in limit less room for the
 // kernels' static shared memory
@@ -741,9 +1100,93 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (band)");
 }
 
+// Streaming plan for a 3x3 layer with 32 output channels: one CTA per
+// (image, 128-pixel strip, segment of L output rows), at most one CTA per SM;
+// false where the segments would be short (the band kernel's edge overhead
+// is then no worse) or the weights and two stages do not fit.
+bool stream_plan(int w, int h, int n, int cin, int nsm, int *L, int *nseg, int *G, int *stages, size_t *smem) {
+    if (w < TC_M || g_tc_variant == 1 || g_tc_variant == 3 || g_tc_variant == 4) return false;
+    if (size_t(9) * cin * 32 * 2 > kBandMaxWeights) return false;
+    const size_t wbytes = size_t(15 * (cin / TC_KC) + 2) * 32 * TC_KC * 2;  // with the zero tiles
+    // the 227 KB per block less this kernel's ~5 KB of static shared memory
+    constexpr size_t kStreamSmemLimit = 221 * 1024;
+    const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
+    if (units > nsm) return false;
+    int segs = int(nsm / units);
+    int l = (h + segs - 1) / segs;
+    l += l & 1;  // even: row pairs never straddle two segments
+    if (l < (g_tc_variant == 5 ? 2 : 16)) return false;
+    *L = l;
+    *nseg = (h + l - 1) / l;
+    // the tallest group (6, 4 or 2 rows) that leaves three stages
+    for (int g = 6; g >= 2; g -= 2) {
+        const size_t blk = (size_t(g) * BAND_PX * 16 + 127) / 128 * 128;
+        const size_t stage = 4 * blk;
+        if (1024 + wbytes + 2 * stage > kStreamSmemLimit) continue;
+        const size_t room = kStreamSmemLimit - 1024 - wbytes;
+        int st = int(room / stage);
+        if (st > ST_SMAX) st = ST_SMAX;
+        if (st < (g > 2 ? 3 : 2)) continue;
+        *G = g;
+        *stages = st;
+        *smem = 1024 + wbytes + size_t(st) * stage;
+        return true;
+    }
+    return false;
+}
+
+glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
+                          const float *bias, void *y, long long ys, int relu, int *err, cudaStream_t st, int L,
+                          int nseg, int G, int stages, size_t smem, void *pool_y = nullptr,
+                          const void *head_w = nullptr, const float *head_b = nullptr, float *head_y = nullptr,
+                          int head_out = 0) {
+    CUtensorMap mA0, mA1;
+    if (!map_act_band(&mA0, x0, c0, w, h, n, G - 2) ||
+        !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, G - 2))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: streaming activation tensor map rejected");
+    StreamArgs a;
+    a.n = n;
+    a.h = h;
+    a.w = w;
+    a.nchunk0 = c0 / TC_KC;
+    a.nchunk = (c0 + c1) / TC_KC;
+    a.nbx = (w + TC_M - 1) / TC_M;
+    a.nseg = nseg;
+    a.L = L;
+    a.stages = stages;
+    a.blk_stride = uint32_t((size_t(G) * BAND_PX * 16 + 127) / 128 * 128);
+    a.stage_bytes = 4 * a.blk_stride;
+    a.tx_bytes = uint32_t(4 * G * BAND_PX * 16);
+    a.wtile = uint32_t(32 * TC_KC * 2);
+    a.bias = bias;
+    a.y = y;
+    a.ys = ys;
+    a.relu = relu ? 1 : 0;
+    a.err = err;
+    a.pool_y = static_cast<__nv_bfloat16 *>(pool_y);
+    a.head_w = static_cast<const __nv_bfloat16 *>(head_w);
+    a.head_b = head_b;
+    a.head_y = head_y;
+    a.head_out = head_out;
+    const auto kern = G == 6 ? k_tc_conv_stream<6> : (G == 4 ? k_tc_conv_stream<4> : k_tc_conv_stream<2>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute (streaming)");
+    const unsigned grid = unsigned((long long)n * a.nbx * nseg);
+    kern<<<grid, ST_THREADS, smem, st>>>(mA0, mA1, mB, a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (streaming)");
+}
+
+int sm_count(int *nsm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev);
+    return e == cudaSuccess ? 0 : 1;
+}
+
 }  // namespace
 
-extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 3) ? variant : 0; }
+extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 5) ? variant : 0; }
 
 extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, int k,
                                        const void *wt, const float *bias, int cout, void *y, long long ys, int relu,
@@ -784,9 +1227,14 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return tcfail(GLBM_EINVAL, "nn_tc_conv: weight tensor map rejected");
     }
-    int R = 0, stages = 0;
+    int nsm = 0;
+    if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv: device query failed");
+    int R = 0, stages = 0, L = 0, nseg = 0, G = 0;
     size_t bsmem = 0;
     int stack = 0;
+    if (k == 3 && !f32_nchw && cout == 32 && stream_plan(w, h, n, cin, nsm, &L, &nseg, &G, &stages, &bsmem))
+        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, y, ys, relu, err, static_cast<cudaStream_t>(stream),
+                             L, nseg, G, stages, bsmem);
     if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem, &stack))
         return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
                            static_cast<cudaStream_t>(stream), R, stages, bsmem, stack);
@@ -810,11 +1258,16 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     a.f32_nchw = f32_nchw ? 1 : 0;
     a.cout_store = f32_nchw ? cout_store : cout;
     a.err = err;
-    const size_t smem = 1024 + size_t(TC_STAGES) * (size_t(mt) * TC_STAGE_A + size_t(cout) * TC_KC * 2);
-    const auto kern = mt == 2 ? k_tc_conv<2> : k_tc_conv<1>;
+    const dim3 grid(unsigned((w + tw - 1) / tw), unsigned(gy), unsigned(n));
+    // a grid of at most one CTA per SM cannot hide latency behind other
+    // CTAs: it keeps more loads in flight with a deep ring instead
+    const bool deep = g_tc_variant != 2 && (long long)grid.x * grid.y * grid.z <= nsm;
+    const int ring = deep ? TC_STAGES_DEEP : TC_STAGES;
+    const size_t smem = 1024 + size_t(ring) * (size_t(mt) * TC_STAGE_A + size_t(cout) * TC_KC * 2);
+    const auto kern = mt == 2 ? (deep ? k_tc_conv<2, TC_STAGES_DEEP> : k_tc_conv<2, TC_STAGES>)
+                              : (deep ? k_tc_conv<1, TC_STAGES_DEEP> : k_tc_conv<1, TC_STAGES>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute");
-    const dim3 grid(unsigned((w + tw - 1) / tw), unsigned(gy), unsigned(n));
     kern<<<grid, TC_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(mA0, mA1, mB, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch");
@@ -826,8 +1279,10 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
                                              int head_out, float *head_y, int *err, void *stream) {
     if (!x0 || !wt || !bias || !err || (c1 > 0 && !x1) || (!y && !pool_y && !head_y))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: x0, wt, bias, err and at least one output are required");
-    if (n < 1 || h < 1 || w < 1 || c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC || cout != 32)
-        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: needs 32 output channels and input channels in multiples of 32");
+    if (n < 1 || h < 1 || w < 1 || c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC || (cout != 32 && cout != 64))
+        return tcfail(GLBM_EINVAL,
+                      "nn_tc_conv_fused: needs 32 or 64 output channels and input channels in multiples of 32");
+    if (cout != 32 && head_y) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the fused head needs 32 output channels");
     if (y && (ys < cout || ys % 8)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: bad output pixel stride");
     if (pool_y && (h % 2 || w % 2)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: pooling needs even h and w");
     if (head_y && (!head_w || !head_b || head_out < 1 || head_out > 4))
@@ -836,10 +1291,15 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
     if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: arrays must be 16-byte aligned");
     if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: cuTensorMapEncodeTiled is not available");
     const int cin = c0 + c1;
-    int R = 0, stages = 0, stack = 0;
+    int R = 0, stages = 0, stack = 0, nsm = 0, L = 0, nseg = 0, G = 0;
     size_t smem = 0;
-    if (!band_plan(3, 0, w, cin, cout, h, &R, &stages, &smem, &stack) || !stack || (pool_y && R % 2))
-        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the layer does not fit the stacked band kernel");
+    if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: device query failed");
+    const bool streaming = cout == 32 && stream_plan(w, h, n, cin, nsm, &L, &nseg, &G, &stages, &smem);
+    if (!streaming && (!band_plan(3, 0, w, cin, cout, h, &R, &stages, &smem, &stack) || (cout == 32 && !stack)))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the layer does not fit the band kernel");
+    if (!streaming && pool_y && R % 2) --R;  // pooling pairs the rows of a band (fewer rows need less memory)
+    if (!streaming && R < 2 && pool_y)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: pooling needs bands of two rows or more");
     CUtensorMap mB;
     {
         const cuuint64_t dims[3] = {cuuint64_t(cin), cuuint64_t(cout), 9};
@@ -851,6 +1311,9 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: weight tensor map rejected");
     }
+    if (streaming)
+        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, y, ys, relu, err, static_cast<cudaStream_t>(stream),
+                             L, nseg, G, stages, smem, pool_y, head_w, head_b, head_y, head_out);
     return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
                        R, stages, smem, stack, pool_y, head_w, head_b, head_y, head_out);
 }
@@ -875,6 +1338,17 @@ extern "C" glbm_status glbm_nn_nchw_to_nhwc(const float *x, int n, int c, int h,
                                                                                    static_cast<uint4 *>(y), c_pad);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_nchw_to_nhwc launch");
+}
+
+extern "C" glbm_status glbm_nn_im2col3_nhwc(const float *x, int n, int c, int h, int w, void *y, int c_pad,
+                                            void *stream) {
+    if (!x || !y || n < 1 || c < 1 || h < 1 || w < 1 || c_pad < 9 * c || c_pad % 8 || (uintptr_t(y) & 15u))
+        return tcfail(GLBM_EINVAL, "nn_im2col3_nhwc: need c_pad >= 9 c, a multiple of 8, and 16-byte aligned y");
+    const long long total = (long long)n * h * w;
+    k_im2col3_nhwc<<<grid_for(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, n, c, h, w,
+                                                                                   static_cast<uint4 *>(y), c_pad);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_im2col3_nhwc launch");
 }
 
 extern "C" glbm_status glbm_nn_pool2_nhwc(const void *x, int n, int c, int h, int w, void *y, void *stream) {

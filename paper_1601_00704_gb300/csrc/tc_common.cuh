@@ -24,6 +24,7 @@ namespace {
 constexpr int TC_M = 128;        // output pixels per tile (UMMA M)
 constexpr int TC_KC = 32;        // input channels per K step: 64-byte rows
 constexpr int TC_STAGES = 3;     // TMA ring depth (2, 3, 4 and 7-8 measured: 3 best, occupancy wins)
+constexpr int TC_STAGES_DEEP = 8; // ring depth of grids with at most one CTA per SM
 constexpr int TC_THREADS = 192;  // warp 0 TMA, warp 1 MMA + TMEM, warps 2-5 epilogue
 constexpr int TC_STAGE_A = TC_M * TC_KC * 2;          // 8 KB
 constexpr long long kWaitCycles = 4ll << 30;          // ~2 s at 2 GHz
@@ -49,11 +50,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// As mbar_try_wait, but a thread whose phase is not yet complete may sleep
+// inside the instruction for up to `ns` nanoseconds (it wakes when the phase
+// completes), so that waiting warps leave their scheduler's issue slots to
+// the warps that work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for the phase with the given parity.  Returns false (without
 // waiting further) once any thread of the CTA has given up.
 __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+// mbar_wait for warps that only wait (the same bound, sleeping between tests).
+__device__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity, volatile int *abort_flag, int *err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             *abort_flag = 1;

@@ -421,6 +421,13 @@ class UNet:
             b = torch.zeros(cop, dtype=torch.float32, device="cuda")
             b[:co] = self.params[ob:ob + co]
             W[name], Bs[name] = wt, b
+            if name == "e0a" and k == 3 and 9 * ci <= 32:
+                # the same weights [co][ci][3][3] read as a 1x1 convolution of the
+                # 3x3 patches (glbm_nn_im2col3_nhwc): [co][9 ci][1][1]
+                wi = torch.empty(cop * 32, dtype=torch.bfloat16, device="cuda")
+                self._ok(self.lib.glbm_nn_tc_pack_weights(_ptr(self.params, ow), co, 9 * ci, 1, cop, 32,
+                                                          C.c_void_p(wi.data_ptr()), self._stream()), "tc_pack")
+                W["e0a_im2col"] = wi
         self._tc = (self._version, W, Bs)
         return self._tc
 
@@ -434,7 +441,7 @@ class UNet:
 
         def z(c, l):
             return torch.empty((n, h >> l, w >> l, c), dtype=torch.bfloat16, device="cuda")
-        B = {"x": z(max(32, self._pad(self.in_ch, 32)), 0)}
+        B = {"x": z(max(32, self._pad(self.in_ch, 32), self._pad(9 * self.in_ch, 32) if 9 * self.in_ch <= 32 else 0), 0)}
         L = self.levels
         for l in range(L):
             c = self.ch[l]
@@ -448,38 +455,58 @@ class UNet:
         self._tc_bufs = {key: B}
         return B
 
-    def _tc_conv(self, B, x0, c0, x1, c1, n, h, w, name, relu, y, head=False):
+    def _tc_conv(self, B, x0, c0, x1, c1, n, h, w, name, relu, y, head=False, wkey=None, k=None):
         _, W, Bs = self._tc
-        k = 1 if head else 3
+        if k is None:
+            k = 1 if head else 3
         cop = Bs[name].numel()
         self._ok(self.lib.glbm_nn_tc_conv(
             C.c_void_p(x0.data_ptr()), c0, C.c_void_p(x1.data_ptr()) if x1 is not None else None, c1,
-            n, h, w, k, C.c_void_p(W[name].data_ptr()), C.c_void_p(Bs[name].data_ptr()), cop,
+            n, h, w, k, C.c_void_p(W[wkey or name].data_ptr()), C.c_void_p(Bs[name].data_ptr()), cop,
             C.c_void_p(y.data_ptr()), cop, int(relu), int(head), self.out_ch if head else 0,
             C.c_void_p(B["err"].data_ptr()), self._stream()), "tc_conv")
 
-    def forward_tc(self, x, fused=True):
+    def forward_tc(self, x, fused=True, im2col=False):
         """The forward pass on the tensor cores: x (n, in_ch, h, w) FP32 CUDA
         tensor -> (n, out_ch, h, w) FP32.  Activations are BF16 NHWC between
         layers, accumulation FP32; the pipeline's error flag is checked.
-        fused: where the first level has 32 channels and rows of >= 128
-        pixels, its 2x2 pooling and the 1x1 head run inside the epilogues of
-        the convolutions before them (glbm_nn_tc_conv_fused)."""
+        fused: each level's 2x2 pooling runs inside the epilogue of the
+        convolution before it where that layer takes the band kernel (32 or
+        64 channels, rows of >= 128 pixels), and with a 32-channel first
+        level the 1x1 head runs inside the last convolution's epilogue
+        (glbm_nn_tc_conv_fused).
+        im2col: with at most 3 input channels the first convolution runs as a
+        1x1 convolution of the 3x3 patches (glbm_nn_im2col3_nhwc), 27 useful
+        channels of 32 instead of 3 of 32 in each of 9 taps (off by default:
+        at 2048^2 the patch tensor and the 1x1 tile convolution took 275 us
+        against 210 us for the padded input and the streaming 3x3 kernel)."""
         n, _, h, w = x.shape
         self._tc_pack()
         B = self._tc_buffers(n, h, w)
         st = self._stream()
         cin = B["x"].shape[3]
-        self._ok(self.lib.glbm_nn_nchw_to_nhwc(_ptr(x), n, self.in_ch, h, w, C.c_void_p(B["x"].data_ptr()),
-                                               cin, st), "nchw_to_nhwc")
+        _, W, _ = self._tc
+        use_i2c = im2col and "e0a_im2col" in W
+        conv = self.lib.glbm_nn_im2col3_nhwc if use_i2c else self.lib.glbm_nn_nchw_to_nhwc
+        self._ok(conv(_ptr(x), n, self.in_ch, h, w, C.c_void_p(B["x"].data_ptr()), cin, st),
+                 "im2col3_nhwc" if use_i2c else "nchw_to_nhwc")
         L = self.levels
         inp = B["x"]
-        fuse0 = fused and self.ch[0] == 32 and w >= 128
+        fuse_head = fused and self.ch[0] == 32 and w >= 128
+
+        def fuse_pool(l):
+            c = self.ch[l]
+            return (fused and l < L - 1 and c in (32, 64) and (w >> l) >= 128
+                    and 9 * c * c * 2 <= 80 * 1024)
+
         for l in range(L):
             hl, wl, c = h >> l, w >> l, self.ch[l]
-            self._tc_conv(B, inp, cin, None, 0, n, hl, wl, f"e{l}a", True, B[f"a{l}"])
-            if l == 0 and fuse0 and L > 1:
-                self._tc_fused(B, B["a0"], c, n, hl, wl, "e0b", y=B["e0"], pool_y=B["p0"])
+            if l == 0 and use_i2c:
+                self._tc_conv(B, inp, cin, None, 0, n, hl, wl, "e0a", True, B["a0"], wkey="e0a_im2col", k=1)
+            else:
+                self._tc_conv(B, inp, cin, None, 0, n, hl, wl, f"e{l}a", True, B[f"a{l}"])
+            if fuse_pool(l):
+                self._tc_fused(B, B[f"a{l}"], c, n, hl, wl, f"e{l}b", c, y=B[f"e{l}"], pool_y=B[f"p{l}"])
             else:
                 self._tc_conv(B, B[f"a{l}"], c, None, 0, n, hl, wl, f"e{l}b", True, B[f"e{l}"])
                 if l < L - 1:
@@ -493,20 +520,20 @@ class UNet:
             self._ok(self.lib.glbm_nn_upsample2_nhwc(C.c_void_p(top.data_ptr()), n, ctop, hl // 2, wl // 2,
                                                      C.c_void_p(B[f"u{l}"].data_ptr()), st), "upsample2_nhwc")
             self._tc_conv(B, B[f"u{l}"], ctop, B[f"e{l}"], c, n, hl, wl, f"d{l}a", True, B[f"da{l}"])
-            if l == 0 and fuse0:
+            if l == 0 and fuse_head:
                 # d0b with the 1x1 head in its epilogue: d0 itself is never stored
-                self._tc_fused(B, B["da0"], c, n, hl, wl, "d0b", head=True)
+                self._tc_fused(B, B["da0"], c, n, hl, wl, "d0b", c, head=True)
                 return B["y"]
             self._tc_conv(B, B[f"da{l}"], c, None, 0, n, hl, wl, f"d{l}b", True, B[f"d{l}"])
             top, ctop = B[f"d{l}"], c
         self._tc_conv(B, top, ctop, None, 0, n, h, w, "head", False, B["y"], head=True)
         return B["y"]
 
-    def _tc_fused(self, B, x0, c0, n, h, w, name, y=None, pool_y=None, head=False):
+    def _tc_fused(self, B, x0, c0, n, h, w, name, cout, y=None, pool_y=None, head=False):
         _, W, Bs = self._tc
         vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
         self._ok(self.lib.glbm_nn_tc_conv_fused(
-            vp(x0), c0, None, 0, n, h, w, vp(W[name]), vp(Bs[name]), 32, vp(y), 32, 1, vp(pool_y),
+            vp(x0), c0, None, 0, n, h, w, vp(W[name]), vp(Bs[name]), cout, vp(y), cout, 1, vp(pool_y),
             vp(W["head"]) if head else None, vp(Bs["head"]) if head else None, self.out_ch if head else 0,
             vp(B["y"]) if head else None, vp(B["err"]), self._stream()), "tc_conv_fused")
 

@@ -57,13 +57,17 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 0, 3])
+@pytest.mark.parametrize("variant", [1, 0, 3, 2, 5])
 @pytest.mark.parametrize("n,h,w,c0,c1,cout,k,relu,head", CASES)
 def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head, variant):
     """Every case on the tile kernel (variant 1), with the per-layer choice
     (variant 0: the band kernel wherever it applies, with the dy taps
-    stacked along N for 32 output channels) and with the band kernel
-    unstacked (variant 3)."""
+    stacked along N for 32 output channels), with the band kernel
+    unstacked (variant 3), with the tile kernel's ring never deepened
+    (variant 2; in the other variants grids of at most one CTA per SM, most
+    of the small cases here, take the 8-stage ring, which the 72 K steps of
+    the 256-channel case wrap nine times) and with the streaming form of the
+    32-channel band layers however short its segments (variant 5)."""
     import torch
     lib = pkg.load()
     lib.glbm_nn_tc_set_variant(variant)
@@ -105,6 +109,76 @@ def test_tc_conv_matches_oracle(pkg, n, h, w, c0, c1, cout, k, relu, head, varia
         # the BF16 output rounding (half an ulp = 2^-9 relative) plus FP32 accumulation
         bound = 2.0 ** -8 * np.abs(ref) + 1e-6 * scale
         assert (np.abs(got - ref) <= bound).all(), np.abs(got - ref).max()
+
+
+def _band_layer(pkg, rng, n, h, w, c0, c1, variant, fused):
+    """One 3x3 layer with 32 output channels and ReLU under the given kernel
+    variant: (output, pooled output or None, head output or None)."""
+    import torch
+    lib = pkg.load()
+    cout, cin = 32, c0 + c1
+    nhwc = torch.from_numpy(rng.normal(size=(n, h, w, cin)).astype(np.float32)).to(torch.bfloat16).cuda()
+    x0 = nhwc[..., :c0].contiguous()
+    x1 = nhwc[..., c0:].contiguous() if c1 else None
+    wf = rng.normal(0.0, np.sqrt(2.0 / (cin * 9)), size=(cout, cin, 3, 3)).astype(np.float32)
+    wt = torch.empty(9 * cout * cin, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_pack_weights(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, cin, 3, cout, cin,
+                                       _vp(wt), _stream()) == 0
+    bdev = torch.from_numpy(rng.normal(0.0, 0.1, size=cout).astype(np.float32)).cuda()
+    hw = torch.from_numpy(rng.normal(0.0, 0.2, size=3 * 32).astype(np.float32)).to(torch.bfloat16).cuda()
+    hb = torch.from_numpy(rng.normal(0.0, 0.1, size=3).astype(np.float32)).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = torch.full((n, h, w, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+    pool = head = None
+    lib.glbm_nn_tc_set_variant(variant)
+    try:
+        if fused:
+            pool = torch.full((n, h // 2, w // 2, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+            head = torch.full((n, 3, h, w), float("nan"), dtype=torch.float32, device="cuda")
+            rc = lib.glbm_nn_tc_conv_fused(_vp(x0), c0, _vp(x1) if x1 is not None else None, c1, n, h, w, _vp(wt),
+                                           _vp(bdev), cout, _vp(y), cout, 1, _vp(pool), _vp(hw), _vp(hb), 3,
+                                           _vp(head), _vp(err), _stream())
+        else:
+            rc = lib.glbm_nn_tc_conv(_vp(x0), c0, _vp(x1) if x1 is not None else None, c1, n, h, w, 3, _vp(wt),
+                                     _vp(bdev), cout, _vp(y), cout, 1, 0, 0, _vp(err), _stream())
+    finally:
+        lib.glbm_nn_tc_set_variant(0)
+    assert rc == 0, lib.glbm_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    return y, pool, head
+
+
+@pytest.mark.parametrize("n,h,w,c0,c1,fused", [
+    (150, 40, 128, 32, 0, True),    # one 40-row segment per image: 42 input rows wrap the 16-slot ring
+    (100, 34, 128, 64, 32, False),  # three chunks from two tensors
+    (70, 35, 200, 32, 0, False),    # odd rows (a half-used last pair), a 72-pixel last strip
+    (1, 300, 2048, 32, 0, True),    # 16 strips x 9 segments of 34 rows (the last 28)
+])
+def test_streaming_conv_matches_band_kernel(pkg, n, h, w, c0, c1, fused):
+    """The streaming form of the 32-channel layers (variant 5) against the
+    stacked band kernel (variant 4), on layers whose segments wrap the TMEM
+    row ring: the same products of the same BF16 values, summed in the same
+    order for one 32-channel chunk and in another chunk order for three, so
+    outputs agree to at most one BF16 ulp (exactly for one chunk, but for
+    rounding differences the tensor core may make between an MMA and the
+    same MMA split along N at the ring's wrap); fused pooling and head
+    likewise."""
+    import torch
+    seed = n * 1000 + h
+    y4, p4, h4 = _band_layer(pkg, np.random.default_rng(seed), n, h, w, c0, c1, 4, fused)
+    y5, p5, h5 = _band_layer(pkg, np.random.default_rng(seed), n, h, w, c0, c1, 5, fused)
+    pairs = [(y4.float(), y5.float())]
+    if fused:
+        pairs += [(p4.float(), p5.float()), (h4, h5)]
+    for a, b in pairs:
+        assert torch.isfinite(b).all()
+        d = (a - b).abs()
+        assert float((d - 2.0 ** -7 * a.abs()).max()) <= 1e-6 * float(a.abs().max()), float(d.max())
+        if c1 == 0:
+            same = float((d == 0).float().mean())
+            print(f"exactly equal: {same:.6f}")
+            assert same > 0.999
 
 
 def test_tc_conv_rejects_bad_shapes(pkg):
@@ -153,6 +227,99 @@ def test_nhwc_layout_kernels(pkg):
     assert torch.equal(up.cpu(), ref_up)
 
 
+def test_im2col3_layout(pkg):
+    """3x3 patches as channels, bit for bit: channel ci * 9 + 3 (dy + 1) +
+    (dx + 1) holds x[ci][y + dy][x + dx], zero outside the image and in the
+    padding channels."""
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(6)
+    n, c, h, w = 2, 3, 7, 11
+    x = rng.normal(size=(n, c, h, w)).astype(np.float32)
+    y = torch.full((n, h, w, 32), float("nan"), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_im2col3_nhwc(_vp(torch.from_numpy(x).cuda()), n, c, h, w, _vp(y), 32, _stream()) == 0
+    xp = np.pad(x, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    expect = np.zeros((n, h, w, 32), dtype=np.float32)
+    for ci in range(c):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                expect[..., ci * 9 + 3 * (dy + 1) + (dx + 1)] = xp[:, ci, 1 + dy:1 + dy + h, 1 + dx:1 + dx + w]
+    assert torch.equal(y.cpu(), torch.from_numpy(expect).to(torch.bfloat16))
+    assert lib.glbm_nn_im2col3_nhwc(_vp(torch.from_numpy(x).cuda()), n, 4, h, w, _vp(y), 32, _stream()) == -1
+
+
+@pytest.mark.parametrize("n,h,w,cin", [(2, 40, 136, 3), (1, 9, 64, 2)])
+def test_first_layer_as_patch_convolution_matches_oracle(pkg, n, h, w, cin):
+    """A 3x3 convolution of a few input channels computed as the 1x1
+    tensor-core convolution of its 3x3 patches, with the FP32 weights
+    [cout][cin][3][3] packed as [cout][9 cin][1][1], against the oracle's
+    3x3 convolution on the same BF16-rounded inputs and weights."""
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(31 + cin)
+    cout = 32
+    x = rng.normal(size=(n, cin, h, w)).astype(np.float32)
+    wf = rng.normal(0.0, np.sqrt(2.0 / (cin * 9)), size=(cout, cin, 3, 3)).astype(np.float32)
+    b = rng.normal(0.0, 0.1, size=cout).astype(np.float32)
+    ref = np.maximum(ou.conv(_bf16(x), _bf16(wf), b.astype(np.float64)), 0.0)
+    patches = torch.empty((n, h, w, 32), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_im2col3_nhwc(_vp(torch.from_numpy(x).cuda()), n, cin, h, w, _vp(patches), 32,
+                                    _stream()) == 0
+    wt = torch.empty(cout * 32, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_pack_weights(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, 9 * cin, 1, cout, 32,
+                                       _vp(wt), _stream()) == 0
+    y = torch.full((n, h, w, cout), float("nan"), dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.glbm_nn_tc_conv(_vp(patches), 32, None, 0, n, h, w, 1, _vp(wt), _vp(torch.from_numpy(b).cuda()),
+                               cout, _vp(y), cout, 1, 0, 0, _vp(err), _stream()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    got = y.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
+    bound = 2.0 ** -8 * np.abs(ref) + 1e-6 * np.abs(ref).max()
+    assert (np.abs(got - ref) <= bound).all(), np.abs(got - ref).max()
+
+
+@pytest.mark.parametrize("h,w,c0,c1", [(16, 256, 64, 0), (6, 384, 32, 32)])
+def test_fused_pool_64_channels_matches_separate_kernels(pkg, h, w, c0, c1):
+    """The band kernel with 64 output channels and the 2x2 pooling in its
+    epilogue writes what the plain band convolution followed by
+    glbm_nn_pool2_nhwc writes, bit for bit (the same FP32 arithmetic on the
+    same BF16 values); a fused head needs 32 output channels."""
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(h * w + c1)
+    n, cout, cin = 2, 64, c0 + c1
+    nhwc = torch.from_numpy(rng.normal(size=(n, h, w, cin)).astype(np.float32)).to(torch.bfloat16).cuda()
+    x0 = nhwc[..., :c0].contiguous()
+    x1 = nhwc[..., c0:].contiguous() if c1 else None
+    wf = rng.normal(0.0, np.sqrt(2.0 / (cin * 9)), size=(cout, cin, 3, 3)).astype(np.float32)
+    wt = torch.empty(9 * cout * cin, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_pack_weights(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, cin, 3, cout, cin,
+                                       _vp(wt), _stream()) == 0
+    bdev = torch.from_numpy(rng.normal(0.0, 0.1, size=cout).astype(np.float32)).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    xp1 = _vp(x1) if x1 is not None else None
+    y0 = torch.empty((n, h, w, cout), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_conv(_vp(x0), c0, xp1, c1, n, h, w, 3, _vp(wt), _vp(bdev), cout, _vp(y0), cout, 1, 0, 0,
+                               _vp(err), _stream()) == 0
+    p0 = torch.empty((n, h // 2, w // 2, cout), dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_pool2_nhwc(_vp(y0), n, cout, h, w, _vp(p0), _stream()) == 0
+    y1 = torch.full_like(y0, float("nan"))
+    p1 = torch.full_like(p0, float("nan"))
+    assert lib.glbm_nn_tc_conv_fused(_vp(x0), c0, xp1, c1, n, h, w, _vp(wt), _vp(bdev), cout, _vp(y1), cout, 1,
+                                     _vp(p1), None, None, 0, None, _vp(err), _stream()) == 0, \
+        lib.glbm_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(y0, y1)
+    assert torch.equal(p0, p1)
+    hw = torch.zeros(4 * 32, dtype=torch.bfloat16, device="cuda")
+    hy = torch.zeros((n, 1, h, w), dtype=torch.float32, device="cuda")
+    assert lib.glbm_nn_tc_conv_fused(_vp(x0), c0, xp1, c1, n, h, w, _vp(wt), _vp(bdev), cout, _vp(y1), cout, 1,
+                                     None, _vp(hw), _vp(bdev), 1, _vp(hy), _vp(err), _stream()) == -1
+    assert b"32 output channels" in lib.glbm_last_error(None)
+
+
 @pytest.mark.parametrize("levels,max_ch,size", [(3, 64, 32), (4, None, 64), (3, 64, 256)])
 def test_unet_forward_tc_matches_fp32(pkg, levels, max_ch, size):
     """Random-initialised network: the tensor-core forward pass agrees with the
@@ -172,8 +339,9 @@ def test_unet_forward_tc_matches_fp32(pkg, levels, max_ch, size):
 
 @pytest.mark.parametrize("levels,size", [(3, 256), (6, 512)])
 def test_unet_forward_tc_fused_matches_unfused(pkg, levels, size):
-    """The fused first level (2x2 pool and 1x1 head inside the band kernel's
-    epilogues) gives what the separate kernels give: the pooled tensor
+    """The fused levels (2x2 pooling inside the band kernel's epilogue at
+    the 32- and 64-channel levels, the 1x1 head inside the last
+    convolution's) give what the separate kernels give: the pooled tensors
     exactly (same arithmetic on the same BF16 values), the network output
     to FP32 summation order."""
     import torch
@@ -181,15 +349,39 @@ def test_unet_forward_tc_fused_matches_unfused(pkg, levels, size):
     net = UNet(base=32, levels=levels, seed=7, max_ch=128)
     rng = np.random.default_rng(17)
     x = torch.from_numpy(rng.normal(size=(2, 3, size, size)).astype(np.float32)).cuda()
-    y0 = net.forward_tc(x, fused=False).clone()
-    p0 = net._tc_bufs[(2, size, size)]["p0"].clone()
-    y1 = net.forward_tc(x, fused=True).clone()
-    p1 = net._tc_bufs[(2, size, size)]["p0"].clone()
+    key = (2, size, size)
+    y0 = net.forward_tc(x, fused=False, im2col=False).clone()
+    p0 = [net._tc_bufs[key][f"p{l}"].clone() for l in (0, 1)]
+    y1 = net.forward_tc(x, fused=True, im2col=False).clone()
+    p1 = [net._tc_bufs[key][f"p{l}"].clone() for l in (0, 1)]
     torch.cuda.synchronize()
     assert net.tc_error() == 0
-    assert torch.equal(p0, p1)
+    for a, b in zip(p0, p1):
+        assert torch.equal(a, b)
     rel = float((y1 - y0).abs().max() / y0.abs().max())
     assert rel < 1e-5, rel
+
+
+def test_unet_forward_tc_first_layer_as_patches(pkg):
+    """The first convolution as the 1x1 convolution of 3x3 patches sums the
+    same BF16 products in another order: its output agrees with the direct
+    3x3 form to about one BF16 ulp, and the network output to well below
+    the BF16 activation error of the pass."""
+    import torch
+    from paper_1601_00704_gb300.surrogate import UNet
+    net = UNet(base=32, levels=4, seed=9, max_ch=128)
+    rng = np.random.default_rng(19)
+    x = torch.from_numpy(rng.normal(size=(1, 3, 256, 256)).astype(np.float32)).cuda()
+    key = (1, 256, 256)
+    y0 = net.forward_tc(x, im2col=False).clone()
+    a0 = net._tc_bufs[key]["a0"].float().clone()
+    y1 = net.forward_tc(x, im2col=True).clone()
+    a1 = net._tc_bufs[key]["a0"].float().clone()
+    torch.cuda.synchronize()
+    assert net.tc_error() == 0
+    assert float((a1 - a0).abs().max()) <= 2.0 ** -7 * float(a0.abs().max())
+    rel = float((y1 - y0).norm() / y0.norm())
+    assert rel < 1e-2, rel
 
 
 def test_trained_network_tc_prediction(pkg):
