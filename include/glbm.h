@@ -474,7 +474,10 @@ glbm_status glbm_nn_adam(float *p, const float *g, float *m, float *v,
 /* y = conv(concat(x0, x1)) + bias, then max(., 0) when relu != 0; zero
  * padding ksize/2 (ksize 1 or 3).  x0 holds c0 channels, x1 (may be NULL
  * when c1 = 0) c1 channels of the same n x h x w images; c0 >= 32 and c1 are
- * multiples of 32.  wt: BF16 [ksize^2][cout][c0 + c1]; bias: cout FP32;
+ * multiples of 32, or c1 = 0 and c0 a multiple of 16 (a first layer of few
+ * input channels padded to 16 rather than 32; the kernels read its last
+ * 32-channel chunk with zeros in place of the missing channels).  wt: BF16
+ * [ksize^2][cout][c0 + c1]; bias: cout FP32;
  * cout a multiple of 16 in [16, 256].  Output: f32_nchw = 0 -> BF16 NHWC at
  * y with pixel stride ys >= cout (a multiple of 8; y may point at a channel
  * slice of a wider tensor); f32_nchw != 0 -> the first cout_store channels
@@ -501,8 +504,8 @@ glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, int c1,
  *           head_b FP32 [head_out], head_out in 1..4, written FP32 NCHW
  *           (n, head_out, h, w).
  * EINVAL when the layer does not fit the band kernel (rows of >= 128 pixels,
- * input channels in multiples of 32, weights within shared memory; with 32
- * output channels the stacked form).
+ * input channels as in glbm_nn_tc_conv, weights within shared memory; with
+ * 32 output channels the stacked or streaming form).
  */
 glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
                                   int c1, int n, int h, int w, const void *wt,

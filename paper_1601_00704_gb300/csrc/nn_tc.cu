@@ -551,6 +551,7 @@ constexpr int ST_SMAX = 12;
 
 struct StreamArgs {
     int n, h, w, nchunk0, nchunk, nbx, nseg, L, stages;
+    int nblk;              // 8-channel blocks per chunk: 4, or 2 for a 16-channel input
     uint32_t blk_stride;   // bytes between the 8-channel blocks of a stage (LBO)
     uint32_t stage_bytes;  // 4 blocks
     uint32_t tx_bytes;     // bytes the 4 TMA loads of a stage deliver
@@ -653,8 +654,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     uint8_t *dst = sA + size_t(s) * a.stage_bytes;
                     const bool first = ch < a.nchunk0;
                     const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
-#pragma unroll
-                    for (int blk = 0; blk < 4; ++blk)
+                    for (int blk = 0; blk < a.nblk; ++blk)
                         tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
                                     x0 - 1, ya - 1 + G * g, img);
                 }
@@ -667,6 +667,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             const uint64_t zdesc = sdesc_nosw(smem_u32(szero), 2048u, 128u);
             const uint64_t wdesc = sdesc_k64(sW);
             const uint32_t wt16 = a.wtile >> 4, kstep = (2 * a.blk_stride) >> 4;
+            const int kks = a.nblk / 2;  // K steps of 16 channels per chunk
             const uint32_t d13 = uint32_t((ST_SLOTS - 3) * 32);
             long long i = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
@@ -704,8 +705,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                             for (int dxi = 0; dxi < 3; ++dxi)
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk)
-                                    umma_bf16(d0, arow + uint64_t(dxi + kk * kstep),
-                                              b0 + uint64_t(5 * dxi * wt16 + kk * 2), id96, 1u);
+                                    if (kk < kks)
+                                        umma_bf16(d0, arow + uint64_t(dxi + kk * kstep),
+                                                  b0 + uint64_t(5 * dxi * wt16 + kk * 2), id96, 1u);
                         } else {
                             // slots 13-15 take B shifted by 1 (s0 = 14: [0 W(+1) W(0)]) or
                             // 2 (s0 = 15: [0 0 W(+1)]) tiles; slots 0-2 the rest, shifted
@@ -715,6 +717,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                             for (int dxi = 0; dxi < 3; ++dxi)
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk) {
+                                    if (kk >= kks) break;
                                     const uint64_t ad = arow + uint64_t(dxi + kk * kstep);
                                     const uint64_t bk = b0 + uint64_t(5 * dxi * wt16 + kk * 2);
                                     umma_bf16(tmem + d13, ad, bk - uint64_t(sh * wt16), id96, 1u);
@@ -1007,6 +1010,9 @@ int g_tc_variant = 0;
 // kernels' static shared memory
 constexpr size_t kSmemLimit = 226 * 1024;
 constexpr size_t kBandMaxWeights = 80 * 1024;  // larger weight sets: tile kernel
+// 32-channel K chunks of c input channels (a last partial chunk of 16: the
+// loads fill its missing channels with zeros)
+inline int kchunks(int c) { return (c + TC_KC - 1) / TC_KC; }
 
 // Band kernel plan for a layer: rows per band and ring stages, or false when
 // the layer does not fit it (3x3, BF16 output, rows of >= 128 pixels,
@@ -1014,7 +1020,7 @@ constexpr size_t kBandMaxWeights = 80 * 1024;  // larger weight sets: tile kerne
 bool band_plan(int k, int f32_nchw, int w, int cin, int cout, int h, int *R, int *stages, size_t *smem,
                int *stack) {
     if (k != 3 || f32_nchw || w < TC_M || cout > 64 || cout % 32) return false;
-    const size_t wbytes = size_t(9) * (cin / TC_KC) * cout * TC_KC * 2;
+    const size_t wbytes = size_t(9) * kchunks(cin) * cout * TC_KC * 2;
     if (wbytes > kBandMaxWeights) return false;
     int row = 32;
     while (row < cout) row <<= 1;
@@ -1057,8 +1063,8 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
     a.n = n;
     a.h = h;
     a.w = w;
-    a.nchunk0 = c0 / TC_KC;
-    a.nchunk = (c0 + c1) / TC_KC;
+    a.nchunk0 = kchunks(c0);
+    a.nchunk = a.nchunk0 + c1 / TC_KC;
     a.cout = cout;
     a.R = R;
     a.stages = stages;
@@ -1107,7 +1113,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 bool stream_plan(int w, int h, int n, int cin, int nsm, int *L, int *nseg, int *G, int *stages, size_t *smem) {
     if (w < TC_M || g_tc_variant == 1 || g_tc_variant == 3 || g_tc_variant == 4) return false;
     if (size_t(9) * cin * 32 * 2 > kBandMaxWeights) return false;
-    const size_t wbytes = size_t(15 * (cin / TC_KC) + 2) * 32 * TC_KC * 2;  // with the zero tiles
+    const size_t wbytes = size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2;  // with the zero tiles
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
     const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
@@ -1148,15 +1154,17 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.n = n;
     a.h = h;
     a.w = w;
-    a.nchunk0 = c0 / TC_KC;
-    a.nchunk = (c0 + c1) / TC_KC;
+    a.nchunk0 = kchunks(c0);
+    a.nchunk = a.nchunk0 + c1 / TC_KC;
+    // 16 input channels: two 8-channel blocks and one K step per tap
+    a.nblk = c0 % TC_KC ? 2 : 4;
     a.nbx = (w + TC_M - 1) / TC_M;
     a.nseg = nseg;
     a.L = L;
     a.stages = stages;
     a.blk_stride = uint32_t((size_t(G) * BAND_PX * 16 + 127) / 128 * 128);
     a.stage_bytes = 4 * a.blk_stride;
-    a.tx_bytes = uint32_t(4 * G * BAND_PX * 16);
+    a.tx_bytes = uint32_t(a.nblk * G * BAND_PX * 16);
     a.wtile = uint32_t(32 * TC_KC * 2);
     a.bias = bias;
     a.y = y;
@@ -1195,8 +1203,9 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
         return tcfail(GLBM_EINVAL, "nn_tc_conv: x0, wt, bias, y, err (and x1 when c1 > 0) are required");
     if (n < 1 || h < 1 || w < 1 || (k != 1 && k != 3))
         return tcfail(GLBM_EINVAL, "nn_tc_conv: need n, h, w >= 1 and k = 1 or 3");
-    if (c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC)
-        return tcfail(GLBM_EINVAL, "nn_tc_conv: input channel counts must be multiples of 32 (c0 >= 32)");
+    if (c0 < 16 || c0 % 16 || c1 < 0 || c1 % TC_KC || (c0 % TC_KC && c1))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv: input channel counts must be multiples of 32 (c0 may be 16, "
+                                   "or any multiple of 16 when c1 = 0)");
     if (cout < 16 || cout > 256 || cout % 16)
         return tcfail(GLBM_EINVAL, "nn_tc_conv: cout must be a multiple of 16 in [16, 256]");
     if (f32_nchw ? (cout_store < 1 || cout_store > cout) : (ys < cout || ys % 8))
@@ -1243,8 +1252,8 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     a.h = h;
     a.w = w;
     a.taps = taps;
-    a.nchunk0 = c0 / TC_KC;
-    a.nchunk = cin / TC_KC;
+    a.nchunk0 = kchunks(c0);
+    a.nchunk = a.nchunk0 + c1 / TC_KC;
     a.cout = cout;
     a.tw = tw;
     a.th = th;
@@ -1279,9 +1288,11 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
                                              int head_out, float *head_y, int *err, void *stream) {
     if (!x0 || !wt || !bias || !err || (c1 > 0 && !x1) || (!y && !pool_y && !head_y))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: x0, wt, bias, err and at least one output are required");
-    if (n < 1 || h < 1 || w < 1 || c0 < TC_KC || c0 % TC_KC || c1 < 0 || c1 % TC_KC || (cout != 32 && cout != 64))
+    if (n < 1 || h < 1 || w < 1 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % TC_KC || (c0 % TC_KC && c1) ||
+        (cout != 32 && cout != 64))
         return tcfail(GLBM_EINVAL,
-                      "nn_tc_conv_fused: needs 32 or 64 output channels and input channels in multiples of 32");
+                      "nn_tc_conv_fused: needs 32 or 64 output channels and input channels in multiples of 32 "
+                      "(c0 may be a multiple of 16 when c1 = 0)");
     if (cout != 32 && head_y) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the fused head needs 32 output channels");
     if (y && (ys < cout || ys % 8)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: bad output pixel stride");
     if (pool_y && (h % 2 || w % 2)) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: pooling needs even h and w");

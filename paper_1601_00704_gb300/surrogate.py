@@ -421,6 +421,12 @@ class UNet:
             b = torch.zeros(cop, dtype=torch.float32, device="cuda")
             b[:co] = self.params[ob:ob + co]
             W[name], Bs[name] = wt, b
+            if name == "e0a" and k == 3 and ci <= 16:
+                # inference reads the network input padded to 16 channels, not 32
+                w16 = torch.empty(9 * cop * 16, dtype=torch.bfloat16, device="cuda")
+                self._ok(self.lib.glbm_nn_tc_pack_weights(_ptr(self.params, ow), co, ci, 3, cop, 16,
+                                                          C.c_void_p(w16.data_ptr()), self._stream()), "tc_pack")
+                W["e0a_c16"] = w16
             if name == "e0a" and k == 3 and 9 * ci <= 32:
                 # the same weights [co][ci][3][3] read as a 1x1 convolution of the
                 # 3x3 patches (glbm_nn_im2col3_nhwc): [co][9 ci][1][1]
@@ -442,6 +448,8 @@ class UNet:
         def z(c, l):
             return torch.empty((n, h >> l, w >> l, c), dtype=torch.bfloat16, device="cuda")
         B = {"x": z(max(32, self._pad(self.in_ch, 32), self._pad(9 * self.in_ch, 32) if 9 * self.in_ch <= 32 else 0), 0)}
+        if self.in_ch <= 16:
+            B["x16"] = z(16, 0)
         L = self.levels
         for l in range(L):
             c = self.ch[l]
@@ -484,14 +492,15 @@ class UNet:
         self._tc_pack()
         B = self._tc_buffers(n, h, w)
         st = self._stream()
-        cin = B["x"].shape[3]
         _, W, _ = self._tc
         use_i2c = im2col and "e0a_im2col" in W
+        use16 = not use_i2c and "e0a_c16" in W
+        inp = B["x16"] if use16 else B["x"]
+        cin = inp.shape[3]
         conv = self.lib.glbm_nn_im2col3_nhwc if use_i2c else self.lib.glbm_nn_nchw_to_nhwc
-        self._ok(conv(_ptr(x), n, self.in_ch, h, w, C.c_void_p(B["x"].data_ptr()), cin, st),
+        self._ok(conv(_ptr(x), n, self.in_ch, h, w, C.c_void_p(inp.data_ptr()), cin, st),
                  "im2col3_nhwc" if use_i2c else "nchw_to_nhwc")
         L = self.levels
-        inp = B["x"]
         fuse_head = fused and self.ch[0] == 32 and w >= 128
 
         def fuse_pool(l):
@@ -503,6 +512,8 @@ class UNet:
             hl, wl, c = h >> l, w >> l, self.ch[l]
             if l == 0 and use_i2c:
                 self._tc_conv(B, inp, cin, None, 0, n, hl, wl, "e0a", True, B["a0"], wkey="e0a_im2col", k=1)
+            elif l == 0 and use16:
+                self._tc_conv(B, inp, cin, None, 0, n, hl, wl, "e0a", True, B["a0"], wkey="e0a_c16")
             else:
                 self._tc_conv(B, inp, cin, None, 0, n, hl, wl, f"e{l}a", True, B[f"a{l}"])
             if fuse_pool(l):

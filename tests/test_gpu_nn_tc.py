@@ -54,6 +54,10 @@ CASES = [
     (1, 8, 2048, 32, 0, 32, 3, True, False),    # one band of 8 rows across 16 pixel tiles
     (1, 640, 128, 32, 0, 32, 3, True, False),   # 160 bands: CTAs reuse both accumulator buffers (stacked)
     (1, 640, 128, 32, 0, 64, 3, False, False),  # 160 bands, 64 output channels (unstacked)
+    # a first layer with 16 input channels (the loads zero-fill the chunk's other 16):
+    (2, 20, 40, 16, 0, 32, 3, True, False),     # tile kernel
+    (1, 24, 256, 16, 0, 32, 3, True, False),    # band / streaming
+    (1, 12, 300, 16, 0, 64, 3, True, False),    # band, 64 output channels
 ]
 
 
@@ -154,6 +158,7 @@ def _band_layer(pkg, rng, n, h, w, c0, c1, variant, fused):
     (100, 34, 128, 64, 32, False),  # three chunks from two tensors
     (70, 35, 200, 32, 0, False),    # odd rows (a half-used last pair), a 72-pixel last strip
     (1, 300, 2048, 32, 0, True),    # 16 strips x 9 segments of 34 rows (the last 28)
+    (100, 34, 128, 16, 0, False),   # a 16-channel input: two blocks and one K step per tap
 ])
 def test_streaming_conv_matches_band_kernel(pkg, n, h, w, c0, c1, fused):
     """The streaming form of the 32-channel layers (variant 5) against the
@@ -191,8 +196,10 @@ def test_tc_conv_rejects_bad_shapes(pkg):
     def call(c0, cout, k):
         return lib.glbm_nn_tc_conv(_vp(buf), c0, None, 0, 1, 4, 4, k, _vp(buf), _vp(b), cout, _vp(buf), cout,
                                    1, 0, 0, _vp(err), _stream())
-    assert call(48, 32, 3) == -1   # input channels not a multiple of 32
+    assert call(40, 32, 3) == -1   # input channels not a multiple of 16
     assert b"multiples of 32" in lib.glbm_last_error(None)
+    assert lib.glbm_nn_tc_conv(_vp(buf), 16, _vp(buf), 32, 1, 4, 4, 3, _vp(buf), _vp(b), 32, _vp(buf), 32,
+                               1, 0, 0, _vp(err), _stream()) == -1  # 16 + 32: chunks would straddle the tensors
     assert call(32, 24, 3) == -1   # cout not a multiple of 16
     assert b"cout" in lib.glbm_last_error(None)
     assert call(32, 32, 5) == -1   # kernel size 5
