@@ -521,7 +521,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     }
 }
 
-// ---- Streaming variant for 32 output channels --------------------------------
+// ---- Streaming variant for 32 and 64 output channels --------------------------
 // The band kernel above clears and drains its accumulator per band of R = 4
 // rows: the stacked MMA of each of the band's R + 2 halo rows also feeds the
 // two rows above and below the band, 1.5x the MMAs the outputs need, and the
@@ -540,6 +540,10 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
 // so that each adds only its part.  The weights of one (chunk, dx) sit as
 // [0 0 W(+1) W(0) W(-1) 0 0] in shared memory, neighbours sharing their
 // zero tiles.
+// With 64 output channels the ring has 8 slots of 64 columns and each input
+// row takes three N = 64 MMAs per tap and K step, one per output row (no
+// stacking, so no ring wrap inside an MMA); groups of two input rows leave
+// the epilogue two groups of slack in the 4 pair slots.
 // Roles: warp 0 TMA (G input rows of one 32-channel chunk per stage: boxes
 // of G rows, as tall as the band kernel's, keep the TMA engine streaming),
 // warp 1 MMA and TMEM, warps 4-7 epilogue (one per lane quarter); every wait
@@ -568,20 +572,23 @@ struct StreamArgs {
     int head_out;
 };
 
-template <int G>
+template <int G, int COUT>
 __global__ void __launch_bounds__(ST_THREADS, 1)
 k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                  const __grid_constant__ CUtensorMap mapB, const StreamArgs a) {
+    constexpr bool STACK = COUT == 32;  // dy taps stacked along N
+    constexpr int NS = 512 / COUT;      // TMEM row slots
+    constexpr int NP = NS / 2;          // row pair slots
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ntile_w = 9 * a.nchunk;
-    const int nslot_w = 15 * a.nchunk + 2;  // weight tiles with their zero tiles
+    const int nslot_w = STACK ? 15 * a.nchunk + 2 : ntile_w;  // stacked: with their zero tiles
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(nslot_w) * a.wtile;
     __shared__ __align__(8) uint64_t full[ST_SMAX], empty[ST_SMAX], wfull, pfull[ST_PAIRS], pempty[ST_PAIRS];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ __align__(16) float sbias[32];
+    __shared__ __align__(16) float sbias[COUT];
     __shared__ float shead[4 * 32], shead_b[4];
     __shared__ __align__(128) uint8_t szero[4096];  // all-zero A (128 rows x 16 K, unswizzled)
 
@@ -593,18 +600,18 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     const int ya = seg * a.L;
     const int Lseg = min(a.L, a.h - ya);
     // input rows ya - 1 .. ya + Lseg (local index ir = 0 .. Lseg + 1), G per
-    // group; output row j (row ya - 2 + j, slot j mod 16) takes input rows
+    // group; output row j (row ya - 2 + j, slot j mod NS) takes input rows
     // j - 2 .. j, so row pair P (j = 2P, 2P + 1) is complete after the group
     // holding input row 2P + 1; pair 0 (rows above the segment) is never
     // stored, pairs 1 .. npairs are
     constexpr int hg = G / 2;
     const int ngroups = (Lseg + 2 + G - 1) / G;
     const int npairs = (Lseg + 1) / 2;
-    if (threadIdx.x < 32) sbias[threadIdx.x] = a.bias[threadIdx.x];
+    if (threadIdx.x < COUT) sbias[threadIdx.x] = a.bias[threadIdx.x];
     if (a.head_y && threadIdx.x < a.head_out * 32) shead[threadIdx.x] = __bfloat162float(a.head_w[threadIdx.x]);
     if (a.head_y && threadIdx.x < a.head_out) shead_b[threadIdx.x] = a.head_b[threadIdx.x];
     for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
-    {
+    if (STACK) {
         // the zero tiles: 0, 1 and 5 + 5k, 6 + 5k around (chunk, dx) group k
         const int per = int(a.wtile / 16);
         for (int j = threadIdx.x; j < nslot_w * per; j += blockDim.x) {
@@ -619,7 +626,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             mbar_init(&empty[s], 1);
         }
         mbar_init(&wfull, 1);
-        for (int p = 0; p < ST_PAIRS; ++p) {
+        for (int p = 0; p < NP; ++p) {
             mbar_init(&pfull[p], 1);
             mbar_init(&pempty[p], 4);  // the four lane-quarter epilogue warps
         }
@@ -638,8 +645,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
             for (int tap = 0; tap < 9; ++tap)
                 for (int ch = 0; ch < a.nchunk; ++ch)
-                    tma_load_3d(sW + size_t(2 + 5 * (ch * 3 + tap % 3) + (2 - tap / 3)) * a.wtile, &mapB, &wfull,
-                                ch * TC_KC, 0, tap);
+                    tma_load_3d(sW + size_t(STACK ? 2 + 5 * (ch * 3 + tap % 3) + (2 - tap / 3) : tap * a.nchunk + ch) *
+                                         a.wtile,
+                                &mapB, &wfull, ch * TC_KC, 0, tap);
             long long i = 0;
             bool go = true;
             for (int g = 0; g < ngroups && go; ++g)
@@ -668,21 +676,26 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             const uint64_t wdesc = sdesc_k64(sW);
             const uint32_t wt16 = a.wtile >> 4, kstep = (2 * a.blk_stride) >> 4;
             const int kks = a.nblk / 2;  // K steps of 16 channels per chunk
-            const uint32_t d13 = uint32_t((ST_SLOTS - 3) * 32);
+            const uint32_t d13 = uint32_t((NS - 3) * 32);
             long long i = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
                 // pairs hg g + 1 .. hg g + hg enter their slots: wait until the
                 // epilogue has drained each one's last stored occupant, then
                 // clear them
                 for (int pn = hg * g + 1; pn <= hg * g + hg && ok; ++pn) {
-                    const int ps = pn % ST_PAIRS, prev = pn - ST_PAIRS;
+                    const int ps = pn % NP, prev = pn - NP;
                     if (prev >= 1 && prev <= npairs &&
-                        !mbar_wait(&pempty[ps], uint32_t((prev - 1) / ST_PAIRS) & 1u, &abort_flag, a.err, 23)) {
+                        !mbar_wait(&pempty[ps], uint32_t((prev - 1) / NP) & 1u, &abort_flag, a.err, 23)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, wdesc, id64, 0u);
+                    if (STACK) {
+                        umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, wdesc, id64, 0u);
+                    } else {
+                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, wdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t((2 * ps + 1) * COUT), zdesc, wdesc, id64, 0u);
+                    }
                 }
                 for (int ch = 0; ch < a.nchunk && ok; ++ch, ++i) {
                     const int s = int(i % S);
@@ -692,14 +705,36 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     }
                     tc_fence_after();
                     const uint64_t a0 = sdesc_nosw(smem_u32(sA + size_t(s) * a.stage_bytes), a.blk_stride, 128u);
+                    if (!STACK) {
+                        // input row G g + ri adds W(dy) to output row G g + ri + 1 - dy
+#pragma unroll 1
+                        for (int ri = 0; ri < G; ++ri) {
+                            const uint64_t arow = a0 + uint64_t(ri * BAND_PX);  // 16-byte units
+#pragma unroll
+                            for (int o = 0; o < 3; ++o) {
+                                const uint32_t d = tmem + uint32_t(((G * g + ri + o) % NS) * COUT);
+#pragma unroll
+                                for (int dxi = 0; dxi < 3; ++dxi) {
+                                    const uint64_t bt = wdesc + uint64_t(((2 - o) * 3 + dxi) * a.nchunk + ch) * wt16;
+#pragma unroll
+                                    for (int kk = 0; kk < 2; ++kk)
+                                        if (kk < kks)
+                                            umma_bf16(d, arow + uint64_t(dxi + kk * kstep), bt + uint64_t(kk * 2),
+                                                      id64, 1u);
+                                }
+                            }
+                        }
+                        umma_commit(&empty[s]);
+                        continue;
+                    }
                     // B of (chunk, dx) group k starts at tile 2 + 5k: [W(+1) W(0) W(-1)]
                     const uint64_t b0 = sdesc_k64(sW) + uint64_t((2 + 15 * ch) * wt16);
 #pragma unroll 1
                     for (int ri = 0; ri < G; ++ri) {
                         // input row G g + ri feeds the slots of rows G g + ri .. + 2
-                        const int s0 = (G * g + ri) % ST_SLOTS;
+                        const int s0 = (G * g + ri) % NS;
                         const uint64_t arow = a0 + uint64_t(ri * BAND_PX);  // 16-byte units
-                        if (s0 <= ST_SLOTS - 3) {
+                        if (s0 <= NS - 3) {
                             const uint32_t d0 = tmem + uint32_t(s0 * 32);
 #pragma unroll
                             for (int dxi = 0; dxi < 3; ++dxi)
@@ -712,7 +747,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                             // slots 13-15 take B shifted by 1 (s0 = 14: [0 W(+1) W(0)]) or
                             // 2 (s0 = 15: [0 0 W(+1)]) tiles; slots 0-2 the rest, shifted
                             // the other way ([W(-1) 0 0] or [W(0) W(-1) 0])
-                            const uint32_t sh = uint32_t(s0 - (ST_SLOTS - 3));  // 1 or 2
+                            const uint32_t sh = uint32_t(s0 - (NS - 3));  // 1 or 2
 #pragma unroll
                             for (int dxi = 0; dxi < 3; ++dxi)
 #pragma unroll
@@ -728,7 +763,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     umma_commit(&empty[s]);
                 }
                 for (int pc = hg * g; pc < hg * g + hg && ok; ++pc)
-                    if (pc >= 1 && pc <= npairs) umma_commit(&pfull[pc % ST_PAIRS]);
+                    if (pc >= 1 && pc <= npairs) umma_commit(&pfull[pc % NP]);
             }
         }
     } else if (warp >= 4) {
@@ -738,92 +773,98 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
         const uint32_t lanes = uint32_t(q * 32) << 16;
         const float4 *sb4 = reinterpret_cast<const float4 *>(sbias);
         for (int P = 1; P <= npairs; ++P) {
-            const int ps = P % ST_PAIRS;
-            if (!mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / ST_PAIRS) & 1u, &abort_flag, a.err, 25)) break;
+            const int ps = P % NP;
+            if (!mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / NP) & 1u, &abort_flag, a.err, 25)) break;
             tc_fence_after();
-            float v[2][32];
-            tmem_ld32x2(tmem + lanes + uint32_t(2 * ps * 32), tmem + lanes + uint32_t((2 * ps + 1) * 32), v[0], v[1]);
-            uint32_t pk[2][16];
-#pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-                const float4 b4 = sb4[j4];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    float x0v = v[u][4 * j4] + b4.x, x1v = v[u][4 * j4 + 1] + b4.y;
-                    float x2v = v[u][4 * j4 + 2] + b4.z, x3v = v[u][4 * j4 + 3] + b4.w;
-                    if (a.relu) {
-                        x0v = fmaxf(x0v, 0.0f);
-                        x1v = fmaxf(x1v, 0.0f);
-                        x2v = fmaxf(x2v, 0.0f);
-                        x3v = fmaxf(x3v, 0.0f);
-                    }
-                    __nv_bfloat162 b0 = __floats2bfloat162_rn(x0v, x1v), b1 = __floats2bfloat162_rn(x2v, x3v);
-                    pk[u][2 * j4] = *reinterpret_cast<uint32_t *>(&b0);
-                    pk[u][2 * j4 + 1] = *reinterpret_cast<uint32_t *>(&b1);
-                }
-            }
             const int r0 = 2 * P - 2;  // segment row of the pair's first row
-            if (a.y && colok) {
+#pragma unroll 1
+            for (int cg = 0; cg < COUT / 32; ++cg) {
+                // 32 channels of both rows of the pair
+                float v[2][32];
+                tmem_ld32x2(tmem + lanes + uint32_t(2 * ps * COUT + cg * 32),
+                            tmem + lanes + uint32_t((2 * ps + 1) * COUT + cg * 32), v[0], v[1]);
+                uint32_t pk[2][16];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (r0 + u >= Lseg) break;
-                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
-                                                           (((long long)img * a.h + ya + r0 + u) * a.w + px) * a.ys);
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const float4 b4 = sb4[cg * 8 + j4];
 #pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4)
-                        dst[j4] = make_uint4(pk[u][4 * j4], pk[u][4 * j4 + 1], pk[u][4 * j4 + 2], pk[u][4 * j4 + 3]);
-                }
-            }
-            if (a.pool_y || a.head_y) {
-                // the fused outputs start from the BF16-rounded values
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pk[u][j]));
-                        v[u][2 * j] = f.x;
-                        v[u][2 * j + 1] = f.y;
-                    }
-            }
-            if (a.head_y) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    if (r0 + u >= Lseg) break;
-                    for (int k = 0; k < a.head_out; ++k) {
-                        float acc_h = 0.0f;
-#pragma unroll
-                        for (int cc = 0; cc < 32; ++cc) acc_h = fmaf(v[u][cc], shead[k * 32 + cc], acc_h);
-                        if (colok)
-                            a.head_y[(((long long)img * a.head_out + k) * a.h + ya + r0 + u) * a.w + px] =
-                                acc_h + shead_b[k];
+                    for (int u = 0; u < 2; ++u) {
+                        float x0v = v[u][4 * j4] + b4.x, x1v = v[u][4 * j4 + 1] + b4.y;
+                        float x2v = v[u][4 * j4 + 2] + b4.z, x3v = v[u][4 * j4 + 3] + b4.w;
+                        if (a.relu) {
+                            x0v = fmaxf(x0v, 0.0f);
+                            x1v = fmaxf(x1v, 0.0f);
+                            x2v = fmaxf(x2v, 0.0f);
+                            x3v = fmaxf(x3v, 0.0f);
+                        }
+                        __nv_bfloat162 b0 = __floats2bfloat162_rn(x0v, x1v), b1 = __floats2bfloat162_rn(x2v, x3v);
+                        pk[u][2 * j4] = *reinterpret_cast<uint32_t *>(&b0);
+                        pk[u][2 * j4 + 1] = *reinterpret_cast<uint32_t *>(&b1);
                     }
                 }
-            }
-            if (a.pool_y) {
-                // rows r0, r0 + 1 (ya and r0 even) and pixels px, px ^ 1 (lanes
-                // lane, lane ^ 1): FP32 ((a + b) + (d + e)) / 4, rounded to BF16
-                const bool wr = (lane & 1) == 0 && colok && r0 + 1 < Lseg;
-                uint32_t pp[16];
+                if (a.y && colok) {
 #pragma unroll
-                for (int cc = 0; cc < 32; cc += 2) {
-                    float s2[2];
+                    for (int u = 0; u < 2; ++u) {
+                        if (r0 + u >= Lseg) break;
+                        uint4 *dst = reinterpret_cast<uint4 *>(
+                            static_cast<__nv_bfloat16 *>(a.y) + (((long long)img * a.h + ya + r0 + u) * a.w + px) * a.ys +
+                            cg * 32);
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float mine_top = v[0][cc + e], mine_bot = v[1][cc + e];
-                        const float nb_top = __shfl_xor_sync(0xffffffffu, mine_top, 1);
-                        const float nb_bot = __shfl_xor_sync(0xffffffffu, mine_bot, 1);
-                        s2[e] = 0.25f * ((mine_top + nb_top) + (mine_bot + nb_bot));
+                        for (int j4 = 0; j4 < 4; ++j4)
+                            dst[j4] = make_uint4(pk[u][4 * j4], pk[u][4 * j4 + 1], pk[u][4 * j4 + 2], pk[u][4 * j4 + 3]);
                     }
-                    __nv_bfloat162 b2 = __floats2bfloat162_rn(s2[0], s2[1]);
-                    pp[cc / 2] = *reinterpret_cast<uint32_t *>(&b2);
                 }
-                if (wr) {
-                    const int pyo = (ya + r0) >> 1;
-                    uint4 *dst = reinterpret_cast<uint4 *>(
-                        a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * 32);
+                if (a.pool_y || (STACK && a.head_y)) {
+                    // the fused outputs start from the BF16-rounded values
 #pragma unroll
-                    for (int j4 = 0; j4 < 4; ++j4)
-                        dst[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&pk[u][j]));
+                            v[u][2 * j] = f.x;
+                            v[u][2 * j + 1] = f.y;
+                        }
+                }
+                if (STACK && a.head_y) {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (r0 + u >= Lseg) break;
+                        for (int k = 0; k < a.head_out; ++k) {
+                            float acc_h = 0.0f;
+#pragma unroll
+                            for (int cc = 0; cc < 32; ++cc) acc_h = fmaf(v[u][cc], shead[k * 32 + cc], acc_h);
+                            if (colok)
+                                a.head_y[(((long long)img * a.head_out + k) * a.h + ya + r0 + u) * a.w + px] =
+                                    acc_h + shead_b[k];
+                        }
+                    }
+                }
+                if (a.pool_y) {
+                    // rows r0, r0 + 1 (ya and r0 even) and pixels px, px ^ 1 (lanes
+                    // lane, lane ^ 1): FP32 ((a + b) + (d + e)) / 4, rounded to BF16
+                    const bool wr = (lane & 1) == 0 && colok && r0 + 1 < Lseg;
+                    uint32_t pp[16];
+#pragma unroll
+                    for (int cc = 0; cc < 32; cc += 2) {
+                        float s2[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float mine_top = v[0][cc + e], mine_bot = v[1][cc + e];
+                            const float nb_top = __shfl_xor_sync(0xffffffffu, mine_top, 1);
+                            const float nb_bot = __shfl_xor_sync(0xffffffffu, mine_bot, 1);
+                            s2[e] = 0.25f * ((mine_top + nb_top) + (mine_bot + nb_bot));
+                        }
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(s2[0], s2[1]);
+                        pp[cc / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                    if (wr) {
+                        const int pyo = (ya + r0) >> 1;
+                        uint4 *dst = reinterpret_cast<uint4 *>(
+                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * COUT + cg * 32);
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4)
+                            dst[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+                    }
                 }
             }
             tc_fence_before();
@@ -1110,10 +1151,14 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 // (image, 128-pixel strip, segment of L output rows), at most one CTA per SM;
 // false where the segments would be short (the band kernel's edge overhead
 // is then no worse) or the weights and two stages do not fit.
-bool stream_plan(int w, int h, int n, int cin, int nsm, int *L, int *nseg, int *G, int *stages, size_t *smem) {
+bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, int *L, int *nseg, int *G, int *stages,
+                 size_t *smem) {
     if (w < TC_M || g_tc_variant == 1 || g_tc_variant == 3 || g_tc_variant == 4) return false;
-    if (size_t(9) * cin * 32 * 2 > kBandMaxWeights) return false;
-    const size_t wbytes = size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2;  // with the zero tiles
+    if (cout != 32 && cout != 64) return false;
+    if (size_t(9) * kchunks(cin) * TC_KC * cout * 2 > kBandMaxWeights) return false;
+    // 32 output channels: the weight tiles with their zero tiles
+    const size_t wbytes = cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
+                                     : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
     const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
@@ -1124,8 +1169,9 @@ bool stream_plan(int w, int h, int n, int cin, int nsm, int *L, int *nseg, int *
     if (l < (g_tc_variant == 5 ? 2 : 16)) return false;
     *L = l;
     *nseg = (h + l - 1) / l;
-    // the tallest group (6, 4 or 2 rows) that leaves three stages
-    for (int g = 6; g >= 2; g -= 2) {
+    // the tallest group (6, 4 or 2 rows) that leaves three stages; with 64
+    // output channels two rows (the 4 pair slots need two groups of slack)
+    for (int g = cout == 32 ? 6 : 2; g >= 2; g -= 2) {
         const size_t blk = (size_t(g) * BAND_PX * 16 + 127) / 128 * 128;
         const size_t stage = 4 * blk;
         if (1024 + wbytes + 2 * stage > kStreamSmemLimit) continue;
@@ -1142,8 +1188,8 @@ bool stream_plan(int w, int h, int n, int cin, int nsm, int *L, int *nseg, int *
 }
 
 glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
-                          const float *bias, void *y, long long ys, int relu, int *err, cudaStream_t st, int L,
-                          int nseg, int G, int stages, size_t smem, void *pool_y = nullptr,
+                          const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
+                          int L, int nseg, int G, int stages, size_t smem, void *pool_y = nullptr,
                           const void *head_w = nullptr, const float *head_b = nullptr, float *head_y = nullptr,
                           int head_out = 0) {
     CUtensorMap mA0, mA1;
@@ -1165,7 +1211,7 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.blk_stride = uint32_t((size_t(G) * BAND_PX * 16 + 127) / 128 * 128);
     a.stage_bytes = 4 * a.blk_stride;
     a.tx_bytes = uint32_t(a.nblk * G * BAND_PX * 16);
-    a.wtile = uint32_t(32 * TC_KC * 2);
+    a.wtile = uint32_t(cout * TC_KC * 2);
     a.bias = bias;
     a.y = y;
     a.ys = ys;
@@ -1176,7 +1222,9 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.head_b = head_b;
     a.head_y = head_y;
     a.head_out = head_out;
-    const auto kern = G == 6 ? k_tc_conv_stream<6> : (G == 4 ? k_tc_conv_stream<4> : k_tc_conv_stream<2>);
+    const auto kern = cout == 64 ? k_tc_conv_stream<2, 64>
+                                 : (G == 6 ? k_tc_conv_stream<6, 32>
+                                           : (G == 4 ? k_tc_conv_stream<4, 32> : k_tc_conv_stream<2, 32>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute (streaming)");
     const unsigned grid = unsigned((long long)n * a.nbx * nseg);
@@ -1241,9 +1289,9 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     int R = 0, stages = 0, L = 0, nseg = 0, G = 0;
     size_t bsmem = 0;
     int stack = 0;
-    if (k == 3 && !f32_nchw && cout == 32 && stream_plan(w, h, n, cin, nsm, &L, &nseg, &G, &stages, &bsmem))
-        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, y, ys, relu, err, static_cast<cudaStream_t>(stream),
-                             L, nseg, G, stages, bsmem);
+    if (k == 3 && !f32_nchw && stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &bsmem))
+        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
+                             static_cast<cudaStream_t>(stream), L, nseg, G, stages, bsmem);
     if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem, &stack))
         return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
                            static_cast<cudaStream_t>(stream), R, stages, bsmem, stack);
@@ -1305,7 +1353,7 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
     int R = 0, stages = 0, stack = 0, nsm = 0, L = 0, nseg = 0, G = 0;
     size_t smem = 0;
     if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: device query failed");
-    const bool streaming = cout == 32 && stream_plan(w, h, n, cin, nsm, &L, &nseg, &G, &stages, &smem);
+    const bool streaming = stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &smem);
     if (!streaming && (!band_plan(3, 0, w, cin, cout, h, &R, &stages, &smem, &stack) || (cout == 32 && !stack)))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the layer does not fit the band kernel");
     if (!streaming && pool_y && R % 2) --R;  // pooling pairs the rows of a band (fewer rows need less memory)
@@ -1323,8 +1371,9 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
             return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: weight tensor map rejected");
     }
     if (streaming)
-        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, y, ys, relu, err, static_cast<cudaStream_t>(stream),
-                             L, nseg, G, stages, smem, pool_y, head_w, head_b, head_y, head_out);
+        return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
+                             static_cast<cudaStream_t>(stream), L, nseg, G, stages, smem, pool_y, head_w, head_b,
+                             head_y, head_out);
     return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
                        R, stages, smem, stack, pool_y, head_w, head_b, head_y, head_out);
 }
