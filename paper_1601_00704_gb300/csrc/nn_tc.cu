@@ -2,9 +2,18 @@
 // on GB300 (sm_103a), plus the NHWC layout kernels around it.
 //
 // The network (a U-Net of 3x3 convolutions) is the library's own addition;
-// the paper has no surrogate.  Its FP32 SIMT kernels (nn.cu) train it and
-// serve as the reference; this file runs the same forward pass on the 5th
-// generation tensor cores:
+// the paper has no surrogate.  Its FP32 SIMT kernels (nn.cu) serve as the
+// reference; this file runs the same convolutions on the 5th generation
+// tensor cores (the training step's weight gradient is in nn_tc_train.cu).
+// Three kernels, chosen per layer by glbm_nn_tc_conv:
+//  * the tile kernel (below): any shape;
+//  * the band kernel: 3x3 layers with 32 or 64 output channels, weights
+//    resident in shared memory, each band's halo loaded once;
+//  * the streaming kernel: the same layers where one CTA per image strip
+//    gets a long segment of rows; it walks down the strip and keeps a ring
+//    of output rows in tensor memory, so each input row is loaded and
+//    multiplied once.
+// The tile kernel:
 //
 //  * activations NHWC in BF16 (pixel stride = the buffer's channel count);
 //    weights BF16 [tap][cout][cin]; FP32 accumulation in tensor memory;
