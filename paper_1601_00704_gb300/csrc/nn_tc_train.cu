@@ -175,24 +175,38 @@ __global__ void k_pack_w_flip(const float *__restrict__ w, int cout, int cin, in
 }
 
 // db[c] += sum over images and pixels of dy (FP32 NCHW, sample stride dybs):
-// block (c, part) sums a slice of channel c's planes, then one atomic.
+// block (c, part) sums a slice of each of channel c's planes in FP32 (float4
+// loads where the plane allows them), the block's warps reduce by shuffles,
+// then one atomic per block.  FP32 throughout: FP64 arithmetic is slow on
+// this GPU, and each thread's share is a few hundred values.
 __global__ void k_bias_grad(const float *__restrict__ dy, long long dybs, int n, long long hw, float *__restrict__ db) {
     const int c = blockIdx.x;
-    const long long total = (long long)n * hw;
-    double s = 0.0;
-    for (long long i = blockIdx.y * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.y * blockDim.x) {
-        const long long img = i / hw, p = i - img * hw;
-        s += dy[img * dybs + (long long)c * hw + p];
+    const long long stride = (long long)gridDim.y * blockDim.x;
+    const long long t0 = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    float s = 0.0f;
+    for (int img = 0; img < n; ++img) {
+        const float *plane = dy + img * dybs + (long long)c * hw;
+        if ((hw & 3) == 0 && (reinterpret_cast<uintptr_t>(plane) & 15) == 0) {
+            const float4 *p4 = reinterpret_cast<const float4 *>(plane);
+            for (long long i = t0; i < hw / 4; i += stride) {
+                const float4 v = p4[i];
+                s += (v.x + v.y) + (v.z + v.w);
+            }
+        } else {
+            for (long long i = t0; i < hw; i += stride) s += plane[i];
+        }
     }
-    __shared__ double sh[256];
-    sh[threadIdx.x] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
-        __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) atomicAdd(&db[c], v);
     }
-    if (threadIdx.x == 0) atomicAdd(&db[c], float(sh[0]));
 }
 
 // NHWC BF16 activations as an MN-major operand: dims (channels, w, h, n),
@@ -278,8 +292,10 @@ extern "C" glbm_status glbm_nn_bias_grad(const float *dy, long long dybs, int c,
     if (!dy || !db || c < 1 || n < 1 || h < 1 || w < 1 || dybs < (long long)c * h * w)
         return tcfail(GLBM_EINVAL, "nn_bias_grad: invalid sizes or pointers");
     const long long hw = (long long)h * w;
+    // about 64 values per thread, and enough blocks for every SM
     long long parts = ((long long)n * hw + 256 * 64 - 1) / (256 * 64);
     if (parts > 1024) parts = 1024;
+    if (parts < 1) parts = 1;
     k_bias_grad<<<dim3(unsigned(c), unsigned(parts)), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, dybs, n, hw, db);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_bias_grad launch");
