@@ -515,6 +515,16 @@ glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
                                   int head_out, float *head_y, int *err,
                                   void *stream);
 
+/* Test hook for the kernels' timeout path: the next tensor-core launch
+ * (glbm_nn_tc_conv, glbm_nn_tc_conv_fused or glbm_nn_tc_conv_wgrad) arms the
+ * TMA barrier of its stage number `stage` (counted from 1 in the first CTA's
+ * ring) but issues none of its copies, so the MMA warp's bounded wait for
+ * that stage runs out after about 2 s.  The kernel then writes its error
+ * code to *err, waits (bounded) for its copies and MMAs in flight, frees its
+ * tensor memory and returns; the CUDA context stays usable.  One launch
+ * takes the setting and clears it; 0 clears it.  Process-wide. */
+void glbm_nn_tc_debug_starve(int stage);
+
 /* Choice of tensor-core convolution kernel for glbm_nn_tc_conv and
  * glbm_nn_tc_conv_fused (process-wide):
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128

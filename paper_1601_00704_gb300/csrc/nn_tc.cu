@@ -36,10 +36,13 @@
 
 #include "tc_common.cuh"
 
+__attribute__((visibility("hidden"))) int g_tc_starve = 0;
+
 namespace {
 
 struct TcConvArgs {
     int n, h, w, taps, nchunk0, nchunk, cout, tw, th;
+    int starve;  // test hook: stage number + 1 the first CTA leaves unloaded
     uint32_t tmem_cols;  // MT accumulators of acc_cols columns
     uint32_t acc_cols;
     const float *bias;
@@ -87,12 +90,14 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
     if (warp == 0) {
         if (lane == 0) {
             const uint32_t bytes = uint32_t(MT * a.tw * a.th * TC_KC * 2 + stage_b);
-            for (int i = 0; i < iters; ++i) {
+            int i = 0;
+            for (; i < iters; ++i) {
                 const int s = i % S, use = i / S;
                 if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 1)) break;
                 const int tap = i / a.nchunk, ch = i - tap * a.nchunk;
                 const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
                 mbar_expect_tx(&full[s], bytes);
+                if (a.starve == i + 1 && blockIdx.x + blockIdx.y + blockIdx.z == 0) continue;
 #pragma unroll
                 for (int t = 0; t < MT; ++t) {
                     uint8_t *dst = sA + (s * MT + t) * TC_STAGE_A;
@@ -104,17 +109,14 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
                 }
                 tma_load_3d(sB + s * stage_b, &mapB, &full[s], ch * TC_KC, 0, tap);
             }
+            drain_ring(full, S, i);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(a.cout);
-            bool ok = true;
             for (int i = 0; i < iters; ++i) {
                 const int s = i % S, use = i / S;
-                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 2)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 2)) break;
                 tc_fence_after();
                 const uint64_t bd = sdesc_k64(sB + s * stage_b);
 #pragma unroll
@@ -127,11 +129,14 @@ k_tc_conv(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUt
                 }
                 umma_commit(&empty[s]);
             }
-            if (ok) umma_commit(&done);
+            umma_commit(&done);  // after a timeout too: the wait below retires every MMA issued
+            mbar_drain(&done, 0);
         }
     } else {
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
-        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 3);
+        // after a timeout the MMA warp still commits `done` (to retire its MMAs):
+        // the accumulator is then not a result
+        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 3) && !abort_flag;
         tc_fence_after();
         for (int t = 0; t < MT && have; ++t) {
             const int m = q * 32 + lane;
@@ -204,6 +209,7 @@ constexpr int BAND_THREADS = 256;
 
 struct BandArgs {
     int n, h, w, nchunk0, nchunk, cout, R, stages;
+    int starve;  // test hook: stage number + 1 the first CTA leaves unloaded
     int nbx, nby;
     long long nbands;
     uint32_t blk_stride;   // bytes between 8-channel blocks of a stage (LBO)
@@ -261,7 +267,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(ntile_w) * a.wtile;
     constexpr int SMAX = 3;
-    __shared__ __align__(8) uint64_t full[SMAX], empty[SMAX], wfull, accfull[2], accempty[2];
+    __shared__ __align__(8) uint64_t full[SMAX], empty[SMAX], wfull, accfull[2], accempty[2], drainbar;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ float sbias[64];
@@ -284,6 +290,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
             mbar_init(&empty[s], 1);
         }
         mbar_init(&wfull, 1);
+        mbar_init(&drainbar, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
             mbar_init(&accempty[b], 4);  // one arrival per epilogue warp
@@ -320,6 +327,7 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                         break;
                     }
                     mbar_expect_tx(&full[s], a.tx_bytes);
+                    if (a.starve == i + 1 && blockIdx.x == 0) continue;
                     uint8_t *dst = sA + size_t(s) * a.stage_bytes;
                     const bool first = ch < a.nchunk0;
                     const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
@@ -329,6 +337,8 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                                     x0 - 1, y0 - 1, img);
                 }
             }
+            mbar_drain(&wfull, 0);
+            drain_ring(full, S, i);
         }
     } else if (warp == 3) {
         if (lane == 0) {
@@ -404,6 +414,8 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
                 if (!ok) break;
                 umma_commit(&accfull[ab]);
             }
+            umma_commit(&drainbar);  // retire every MMA issued, also after a timeout
+            mbar_drain(&drainbar, 0);
         }
     } else if (warp >= 4) {
         // Epilogue: per output row one TMEM load of the pixel's channels (32
@@ -564,6 +576,7 @@ constexpr int ST_SMAX = 12;
 
 struct StreamArgs {
     int n, h, w, nchunk0, nchunk, nbx, nseg, L, stages;
+    int starve;  // test hook: stage number + 1 the first CTA leaves unloaded
     int nblk;              // 8-channel blocks per chunk: 4, or 2 for a 16-channel input
     uint32_t blk_stride;   // bytes between the 8-channel blocks of a stage (LBO)
     uint32_t stage_bytes;  // 4 blocks
@@ -594,7 +607,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     const int nslot_w = STACK ? 15 * a.nchunk + 2 : ntile_w;  // stacked: with their zero tiles
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(nslot_w) * a.wtile;
-    __shared__ __align__(8) uint64_t full[ST_SMAX], empty[ST_SMAX], wfull, pfull[ST_PAIRS], pempty[ST_PAIRS];
+    __shared__ __align__(8) uint64_t full[ST_SMAX], empty[ST_SMAX], wfull, pfull[ST_PAIRS], pempty[ST_PAIRS], drainbar;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ __align__(16) float sbias[COUT];
@@ -635,6 +648,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             mbar_init(&empty[s], 1);
         }
         mbar_init(&wfull, 1);
+        mbar_init(&drainbar, 1);
         for (int p = 0; p < NP; ++p) {
             mbar_init(&pfull[p], 1);
             mbar_init(&pempty[p], 4);  // the four lane-quarter epilogue warps
@@ -668,6 +682,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                         break;
                     }
                     mbar_expect_tx(&full[s], a.tx_bytes);
+                    if (a.starve == i + 1 && blockIdx.x == 0) continue;
                     uint8_t *dst = sA + size_t(s) * a.stage_bytes;
                     const bool first = ch < a.nchunk0;
                     const int c0 = (first ? ch : ch - a.nchunk0) * TC_KC;
@@ -675,6 +690,8 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                         tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
                                     x0 - 1, ya - 1 + G * g, img);
                 }
+            mbar_drain(&wfull, 0);
+            drain_ring(full, S, i);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -774,6 +791,8 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                 for (int pc = hg * g; pc < hg * g + hg && ok; ++pc)
                     if (pc >= 1 && pc <= npairs) umma_commit(&pfull[pc % NP]);
             }
+            umma_commit(&drainbar);  // retire every MMA issued, also after a timeout
+            mbar_drain(&drainbar, 0);
         }
     } else if (warp >= 4) {
         const int q = warp & 3;  // TMEM lanes 32q..32q+31 belong to this warp
@@ -1106,6 +1125,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
         !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, R))
         return tcfail(GLBM_EINVAL, "nn_tc_conv: band activation tensor map rejected");
     BandArgs a;
+    a.starve = take_starve();
     a.x0 = static_cast<const __nv_bfloat16 *>(x0);
     a.x1 = static_cast<const __nv_bfloat16 *>(c1 > 0 ? x1 : x0);
     a.c0 = c0;
@@ -1206,6 +1226,7 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
         !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, G - 2))
         return tcfail(GLBM_EINVAL, "nn_tc_conv: streaming activation tensor map rejected");
     StreamArgs a;
+    a.starve = take_starve();
     a.n = n;
     a.h = h;
     a.w = w;
@@ -1250,6 +1271,8 @@ int sm_count(int *nsm) {
 }
 
 }  // namespace
+
+extern "C" void glbm_nn_tc_debug_starve(int stage) { g_tc_starve = stage > 0 ? stage : 0; }
 
 extern "C" void glbm_nn_tc_set_variant(int variant) { g_tc_variant = (variant >= 0 && variant <= 5) ? variant : 0; }
 
@@ -1305,6 +1328,7 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
         return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
                            static_cast<cudaStream_t>(stream), R, stages, bsmem, stack);
     TcConvArgs a;
+    a.starve = take_starve();
     a.n = n;
     a.h = h;
     a.w = w;

@@ -34,6 +34,7 @@ constexpr int WG_THREADS = 192;
 constexpr int WG_BOX = WG_KP * 64;  // bytes of one 32-channel x 32-pixel box
 
 struct WgradArgs {
+    int starve;                  // test hook: stage number + 1 the first CTA leaves unloaded
     int n, h, w, k, nchunk, nf;  // nf = k*k*nchunk (tap, chunk) boxes
     int cin, cout, cy;           // real input / output channels, dy channels (multiple of 32)
     int rows_per_cta;            // split-K: image rows (over n*h) per CTA
@@ -89,7 +90,8 @@ k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int i = 0; i < iters; ++i) {
+            int i = 0;
+            for (; i < iters; ++i) {
                 const int s = i % WG_STAGES, use = i / WG_STAGES;
                 if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, &abort_flag, a.err, 21)) break;
                 const long long row = row0 + i / a.xsteps;
@@ -99,6 +101,7 @@ k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
                 int nload = 0;
                 for (int j = 0; j < 4; ++j) nload += (mtile * 4 + j < a.nf) ? 1 : 0;
                 mbar_expect_tx(&full[s], uint32_t(nload + nb) * WG_BOX);
+                if (a.starve == i + 1 && blockIdx.x + blockIdx.y == 0) continue;
                 for (int j = 0; j < 4; ++j) {
                     const int f = mtile * 4 + j;
                     if (f >= a.nf) break;
@@ -108,17 +111,14 @@ k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
                 }
                 for (int b = 0; b < nb; ++b) tma_load_4d(st + (4 + b) * WG_BOX, &mapDY, &full[s], b * 32, x0, y, img);
             }
+            drain_ring(full, WG_STAGES, i);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16_mn(128, a.cy);
-            bool ok = true;
             for (int i = 0; i < iters; ++i) {
                 const int s = i % WG_STAGES, use = i / WG_STAGES;
-                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 22)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&full[s], use & 1, &abort_flag, a.err, 22)) break;
                 tc_fence_after();
                 uint8_t *st = smem + size_t(s) * a.stage_bytes;
 #pragma unroll
@@ -129,12 +129,15 @@ k_tc_wgrad(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
                 }
                 umma_commit(&empty[s]);
             }
-            if (ok && iters > 0) umma_commit(&done);
+            umma_commit(&done);  // after a timeout too: the wait below retires every MMA issued
+            mbar_drain(&done, 0);
         }
     } else if (iters > 0) {
         const int q = warp & 3;  // TMEM lanes 32q..: box q of this M tile
         const int f = mtile * 4 + q;
-        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 23);
+        // after a timeout the MMA warp still commits `done` (to retire its MMAs):
+        // the accumulator is then not a result
+        const bool have = mbar_wait(&done, 0, &abort_flag, a.err, 23) && !abort_flag;
         tc_fence_after();
         const int tap = f / a.nchunk, ch = f - tap * a.nchunk;
         const int c = ch * 32 + lane;
@@ -237,6 +240,7 @@ extern "C" glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin, con
     if (!map_wgrad(&mX, x, cx, w, h, n) || !map_wgrad(&mDY, dy, cy, w, h, n))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_wgrad: tensor map rejected");
     WgradArgs a;
+    a.starve = take_starve();
     a.n = n;
     a.h = h;
     a.w = w;

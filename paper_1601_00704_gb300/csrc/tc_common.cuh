@@ -19,6 +19,9 @@
 
 extern __attribute__((visibility("hidden"))) thread_local char g_create_err[512];
 
+// defined in nn_tc.cu, library-internal
+extern int g_tc_starve;
+
 namespace {
 
 constexpr int TC_M = 128;        // output pixels per tile (UMMA M)
@@ -89,6 +92,30 @@ __device__ bool mbar_wait_idle(uint64_t *bar, uint32_t parity, volatile int *abo
         }
     }
     return true;
+}
+
+// Teardown: wait, bounded and whatever the abort flag says, for a phase
+// that work already in flight completes (TMA copies landing in shared memory,
+// MMAs retiring), so that none of it outlives the CTA's shared or tensor
+// memory after a timeout.  In a run without a timeout the phase has long
+// completed and the test passes at once.
+__device__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return;
+}
+// The copies of the last min(S, issued) stage loads of an S-stage ring (no
+// later load went into those stages, so their phases are the latest).
+__device__ void drain_ring(uint64_t *full, int S, long long issued) {
+    for (long long u = issued > S ? issued - S : 0; u < issued; ++u) mbar_drain(&full[u % S], uint32_t(u / S) & 1u);
+}
+
+// Test hook (glbm_nn_tc_debug_starve): stage number + 1 whose copies the
+// first CTA of the next tensor-core launch leaves unissued, 0 for none.
+inline int take_starve() {
+    const int s = g_tc_starve;
+    g_tc_starve = 0;
+    return s;
 }
 
 // ---- TMA --------------------------------------------------------------------
