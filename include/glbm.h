@@ -515,6 +515,22 @@ glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void *x1,
                                   int head_out, float *head_y, int *err,
                                   void *stream);
 
+/* As glbm_nn_tc_conv (3x3, BF16 output, bias and ReLU when relu != 0) for a
+ * layer with 32 or 64 output channels, but written 2x nearest-upsampled:
+ * y is BF16 NHWC (n, 2h, 2w) with pixel stride ys >= cout (a multiple of
+ * 8), and each output pixel (r, x) of the convolution fills (2r + a, 2x + b)
+ * for a, b in {0, 1} -- what glbm_nn_upsample2_nhwc would make of the plain
+ * output, without the plain output or the extra pass.  Runs on the
+ * streaming kernel only (its epilogue stages each finished row pair in
+ * shared memory and writes it with four TMA stores per row); EINVAL when
+ * the layer does not fit it (rows of >= 128 pixels, segments of >= 16 rows
+ * per SM, weights within shared memory). */
+glbm_status glbm_nn_tc_conv_up2(const void *x0, int c0, const void *x1,
+                                int c1, int n, int h, int w, const void *wt,
+                                const float *bias, int cout, void *y,
+                                long long ys, int relu, int *err,
+                                void *stream);
+
 /* Test hook for the kernels' timeout path: the next tensor-core launch
  * (glbm_nn_tc_conv, glbm_nn_tc_conv_fused or glbm_nn_tc_conv_wgrad) arms the
  * TMA barrier of its stage number `stage` (counted from 1 in the first CTA's

@@ -49,7 +49,7 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_nn_relu_bwd", "glbm_nn_copy_channels", "glbm_nn_pool2",
            "glbm_nn_upsample2", "glbm_nn_mse", "glbm_nn_adam", "glbm_em_gmm1d",
            "glbm_nn_tc_conv", "glbm_nn_tc_pack_weights", "glbm_nn_nchw_to_nhwc", "glbm_nn_im2col3_nhwc",
-           "glbm_nn_tc_debug_starve",
+           "glbm_nn_tc_debug_starve", "glbm_nn_tc_conv_up2",
            "glbm_nn_pool2_nhwc", "glbm_nn_upsample2_nhwc", "glbm_nn_warm_features",
            "glbm_nn_warm_decode"]
 
@@ -96,6 +96,7 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_batch_set_convergence": ([h, i], i),
         "glbm_nn_tc_set_variant": ([i], None),
         "glbm_nn_tc_debug_starve": ([i], None),
+        "glbm_nn_tc_conv_up2": ([_VP, i, _VP, i, i, i, i, _VP, _VP, i, _VP, ll, i, _VP, _VP], i),
         "glbm_nn_tc_conv_wgrad": ([_VP, i, i, _VP, i, i, i, i, i, i, _VP, _VP, _VP], i),
         "glbm_nn_tc_pack_weights_flip": ([_VP, i, i, i, i, i, i, _VP, _VP], i),
         "glbm_nn_bias_grad": ([_VP, ll, i, i, i, i, _VP, _VP], i),

@@ -592,12 +592,17 @@ struct StreamArgs {
     const float *head_b;
     float *head_y;
     int head_out;
+    // 1: the output goes 2x nearest-upsampled to y by TMA stores (mapY0 /
+    // mapY1: even / odd output columns) from a staged row pair; y unused
+    int up2;
+    uint32_t stage_y_bytes;  // one staged row: 128 pixels x COUT BF16
 };
 
 template <int G, int COUT>
 __global__ void __launch_bounds__(ST_THREADS, 1)
 k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
-                 const __grid_constant__ CUtensorMap mapB, const StreamArgs a) {
+                 const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapY0,
+                 const __grid_constant__ CUtensorMap mapY1, const StreamArgs a) {
     constexpr bool STACK = COUT == 32;  // dy taps stacked along N
     constexpr int NS = 512 / COUT;      // TMEM row slots
     constexpr int NP = NS / 2;          // row pair slots
@@ -607,6 +612,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     const int nslot_w = STACK ? 15 * a.nchunk + 2 : ntile_w;  // stacked: with their zero tiles
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(nslot_w) * a.wtile;
+    // up2: two buffers of a staged row pair after the stages
+    uint8_t *sY = sA + size_t(a.stages) * a.stage_bytes;
+    __shared__ int s_bad;  // up2: an epilogue wait gave up (all four warps leave together)
     __shared__ __align__(8) uint64_t full[ST_SMAX], empty[ST_SMAX], wfull, pfull[ST_PAIRS], pempty[ST_PAIRS], drainbar;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
@@ -654,6 +662,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             mbar_init(&pempty[p], 4);  // the four lane-quarter epilogue warps
         }
         abort_flag = 0;
+        s_bad = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(&tmem_base, 512);
@@ -802,7 +811,21 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
         const float4 *sb4 = reinterpret_cast<const float4 *>(sbias);
         for (int P = 1; P <= npairs; ++P) {
             const int ps = P % NP;
-            if (!mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / NP) & 1u, &abort_flag, a.err, 25)) break;
+            const bool got = mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / NP) & 1u, &abort_flag, a.err, 25);
+            uint8_t *stg = sY + size_t(P & 1) * 2 * a.stage_y_bytes;
+            if (a.up2) {
+                // the four warps agree before the named barriers below, so that a
+                // wait that gave up can never leave a warp waiting at one of them
+                if (!got) s_bad = 1;
+                // the stores issued two pairs ago from this buffer have read it
+                if (warp == 4 && lane == 0) bulk_wait_read1();
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                const int bad = s_bad;
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (bad) break;
+            } else if (!got) {
+                break;
+            }
             tc_fence_after();
             const int r0 = 2 * P - 2;  // segment row of the pair's first row
 #pragma unroll 1
@@ -830,7 +853,17 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                         pk[u][2 * j4 + 1] = *reinterpret_cast<uint32_t *>(&b1);
                     }
                 }
-                if (a.y && colok) {
+                if (a.up2) {
+                    // staged row u: [128 pixels][COUT channels]
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        uint4 *dst = reinterpret_cast<uint4 *>(stg + size_t(u) * a.stage_y_bytes +
+                                                               size_t(q * 32 + lane) * COUT * 2 + cg * 64);
+#pragma unroll
+                        for (int j4 = 0; j4 < 4; ++j4)
+                            dst[j4] = make_uint4(pk[u][4 * j4], pk[u][4 * j4 + 1], pk[u][4 * j4 + 2], pk[u][4 * j4 + 3]);
+                    }
+                } else if (a.y && colok) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (r0 + u >= Lseg) break;
@@ -898,7 +931,24 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
             tc_fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&pempty[ps])) : "memory");
+            if (a.up2) {
+                // the staged pair -> output rows 2y, 2y + 1, even and odd columns
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (warp == 4 && lane == 0) {
+                    for (int u = 0; u < 2 && r0 + u < Lseg; ++u) {
+                        const int yo = (img * a.h + ya + r0 + u) * 2;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            tma_store_3d(&mapY0, stg + size_t(u) * a.stage_y_bytes, 0, x0, yo + e);
+                            tma_store_3d(&mapY1, stg + size_t(u) * a.stage_y_bytes, 0, x0, yo + e);
+                        }
+                    }
+                    bulk_commit();
+                }
+            }
         }
+        if (a.up2 && warp == 4 && lane == 0) bulk_wait_all();
     }
     tc_fence_before();
     __syncthreads();
@@ -1181,13 +1231,15 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 // false where the segments would be short (the band kernel's edge overhead
 // is then no worse) or the weights and two stages do not fit.
 bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, int *L, int *nseg, int *G, int *stages,
-                 size_t *smem) {
+                 size_t *smem, bool up2 = false) {
     if (w < TC_M || g_tc_variant == 1 || g_tc_variant == 3 || g_tc_variant == 4) return false;
     if (cout != 32 && cout != 64) return false;
     if (size_t(9) * kchunks(cin) * TC_KC * cout * 2 > kBandMaxWeights) return false;
     // 32 output channels: the weight tiles with their zero tiles
-    const size_t wbytes = cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
-                                     : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
+    // (with up2 also two staged row pairs: 2 x 2 x 128 pixels x cout BF16)
+    const size_t wbytes = (cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
+                                      : size_t(9) * kchunks(cin) * cout * TC_KC * 2) +
+                          (up2 ? size_t(4) * TC_M * cout * 2 : 0);
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
     const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
@@ -1220,8 +1272,23 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
                           const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
                           int L, int nseg, int G, int stages, size_t smem, void *pool_y = nullptr,
                           const void *head_w = nullptr, const float *head_b = nullptr, float *head_y = nullptr,
-                          int head_out = 0) {
-    CUtensorMap mA0, mA1;
+                          int head_out = 0, bool up2 = false) {
+    CUtensorMap mA0, mA1, mY0, mY1;
+    if (up2) {
+        // y (n, 2h, 2w, ys): output column 2j + e of full row r is element
+        // (c, j, r) of map e, whose pixel stride is two pixels
+        for (int e = 0; e < 2; ++e) {
+            const cuuint64_t dims[3] = {cuuint64_t(cout), cuuint64_t(w), cuuint64_t(2) * h * n};
+            const cuuint64_t strides[2] = {cuuint64_t(ys) * 2 * 2, cuuint64_t(ys) * 2 * 2 * w};
+            const cuuint32_t box[3] = {cuuint32_t(cout), cuuint32_t(TC_M), 1};
+            const cuuint32_t es[3] = {1, 1, 1};
+            if (encode_fn()(e ? &mY1 : &mY0, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                            static_cast<__nv_bfloat16 *>(y) + e * ys, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: output tensor map rejected");
+        }
+    }
     if (!map_act_band(&mA0, x0, c0, w, h, n, G - 2) ||
         !map_act_band(&mA1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, w, h, n, G - 2))
         return tcfail(GLBM_EINVAL, "nn_tc_conv: streaming activation tensor map rejected");
@@ -1252,13 +1319,20 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.head_b = head_b;
     a.head_y = head_y;
     a.head_out = head_out;
+    a.up2 = up2 ? 1 : 0;
+    a.stage_y_bytes = uint32_t(TC_M * cout * 2);
+    if (up2) a.y = nullptr;
+    if (!up2) {
+        mY0 = mA0;  // unused
+        mY1 = mA0;
+    }
     const auto kern = cout == 64 ? k_tc_conv_stream<2, 64>
                                  : (G == 6 ? k_tc_conv_stream<6, 32>
                                            : (G == 4 ? k_tc_conv_stream<4, 32> : k_tc_conv_stream<2, 32>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute (streaming)");
     const unsigned grid = unsigned((long long)n * a.nbx * nseg);
-    kern<<<grid, ST_THREADS, smem, st>>>(mA0, mA1, mB, a);
+    kern<<<grid, ST_THREADS, smem, st>>>(mA0, mA1, mB, mY0, mY1, a);
     e = cudaGetLastError();
     return e == cudaSuccess ? GLBM_OK : tccuda(e, "nn_tc_conv launch (streaming)");
 }
@@ -1409,6 +1483,39 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
                              head_y, head_out);
     return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
                        R, stages, smem, stack, pool_y, head_w, head_b, head_y, head_out);
+}
+
+extern "C" glbm_status glbm_nn_tc_conv_up2(const void *x0, int c0, const void *x1, int c1, int n, int h, int w,
+                                           const void *wt, const float *bias, int cout, void *y, long long ys,
+                                           int relu, int *err, void *stream) {
+    if (!x0 || !wt || !bias || !y || !err || (c1 > 0 && !x1))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: x0, wt, bias, y, err (and x1 when c1 > 0) are required");
+    if (n < 1 || h < 1 || w < 1 || c0 < 16 || c0 % 16 || c1 < 0 || c1 % TC_KC || (c0 % TC_KC && c1) ||
+        (cout != 32 && cout != 64) || ys < cout || ys % 8)
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: needs 32 or 64 output channels, input channels as in "
+                                   "glbm_nn_tc_conv and a pixel stride ys >= cout, a multiple of 8");
+    const uintptr_t mis = (uintptr_t(x0) | uintptr_t(x1) | uintptr_t(wt) | uintptr_t(y)) & 15u;
+    if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: arrays must be 16-byte aligned");
+    if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_up2: cuTensorMapEncodeTiled is not available");
+    const int cin = c0 + c1;
+    int nsm = 0, L = 0, nseg = 0, G = 0, stages = 0;
+    size_t smem = 0;
+    if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv_up2: device query failed");
+    if (!stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &smem, true))
+        return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: the layer does not fit the streaming kernel");
+    CUtensorMap mB;
+    {
+        const cuuint64_t dims[3] = {cuuint64_t(cin), cuuint64_t(cout), 9};
+        const cuuint64_t strides[2] = {cuuint64_t(cin) * 2, cuuint64_t(cin) * 2 * cout};
+        const cuuint32_t box[3] = {TC_KC, cuuint32_t(cout), 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        if (encode_fn()(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(wt), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: weight tensor map rejected");
+    }
+    return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
+                         L, nseg, G, stages, smem, nullptr, nullptr, nullptr, nullptr, 0, true);
 }
 
 extern "C" glbm_status glbm_nn_tc_pack_weights(const float *wf, int cout, int cin, int k, int cout_pad,

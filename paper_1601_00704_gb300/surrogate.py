@@ -480,9 +480,11 @@ class UNet:
         layers, accumulation FP32; the pipeline's error flag is checked.
         fused: each level's 2x2 pooling runs inside the epilogue of the
         convolution before it where that layer takes the band kernel (32 or
-        64 channels, rows of >= 128 pixels), and with a 32-channel first
-        level the 1x1 head runs inside the last convolution's epilogue
-        (glbm_nn_tc_conv_fused).
+        64 channels, rows of >= 128 pixels), a decoder level's 2x upsampling
+        inside the epilogue of the convolution that makes its input where
+        the streaming kernel takes that layer (glbm_nn_tc_conv_up2), and with
+        a 32-channel first level the 1x1 head runs inside the last
+        convolution's epilogue (glbm_nn_tc_conv_fused).
         im2col: with at most 3 input channels the first convolution runs as a
         1x1 convolution of the 3x3 patches (glbm_nn_im2col3_nhwc), 27 useful
         channels of 32 instead of 3 of 32 in each of 9 taps (off by default:
@@ -526,16 +528,32 @@ class UNet:
             if l < L - 1:
                 inp, cin = B[f"p{l}"], c
         top, ctop = B[f"e{L - 1}"], self.ch[L - 1]
+        upsampled = False  # the previous convolution wrote u{l} itself
         for l in range(L - 2, -1, -1):
             hl, wl, c = h >> l, w >> l, self.ch[l]
-            self._ok(self.lib.glbm_nn_upsample2_nhwc(C.c_void_p(top.data_ptr()), n, ctop, hl // 2, wl // 2,
-                                                     C.c_void_p(B[f"u{l}"].data_ptr()), st), "upsample2_nhwc")
+            if not upsampled:
+                self._ok(self.lib.glbm_nn_upsample2_nhwc(C.c_void_p(top.data_ptr()), n, ctop, hl // 2, wl // 2,
+                                                         C.c_void_p(B[f"u{l}"].data_ptr()), st), "upsample2_nhwc")
             self._tc_conv(B, B[f"u{l}"], ctop, B[f"e{l}"], c, n, hl, wl, f"d{l}a", True, B[f"da{l}"])
             if l == 0 and fuse_head:
                 # d0b with the 1x1 head in its epilogue: d0 itself is never stored
                 self._tc_fused(B, B["da0"], c, n, hl, wl, "d0b", c, head=True)
                 return B["y"]
-            self._tc_conv(B, B[f"da{l}"], c, None, 0, n, hl, wl, f"d{l}b", True, B[f"d{l}"])
+            upsampled = False
+            if fused and l > 0 and c in (32, 64):
+                # d{l}b writes the next level's upsampled input directly, where the
+                # streaming kernel takes the layer (otherwise EINVAL: do it apart)
+                _, W, Bs = self._tc
+                rc = self.lib.glbm_nn_tc_conv_up2(
+                    C.c_void_p(B[f"da{l}"].data_ptr()), c, None, 0, n, hl, wl, C.c_void_p(W[f"d{l}b"].data_ptr()),
+                    C.c_void_p(Bs[f"d{l}b"].data_ptr()), c, C.c_void_p(B[f"u{l - 1}"].data_ptr()), c, 1,
+                    C.c_void_p(B["err"].data_ptr()), st)
+                if rc == 0:
+                    upsampled = True
+                elif rc != -1:
+                    self._ok(rc, "tc_conv_up2")
+            if not upsampled:
+                self._tc_conv(B, B[f"da{l}"], c, None, 0, n, hl, wl, f"d{l}b", True, B[f"d{l}"])
             top, ctop = B[f"d{l}"], c
         self._tc_conv(B, top, ctop, None, 0, n, h, w, "head", False, B["y"], head=True)
         return B["y"]

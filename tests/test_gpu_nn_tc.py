@@ -198,6 +198,66 @@ def test_streaming_conv_matches_band_kernel(pkg, n, h, w, c0, c1, fused, cout):
             assert same > 0.999
 
 
+@pytest.mark.parametrize("n,h,w,c0,c1,cout,extra", [
+    (2, 20, 136, 32, 0, 32, 0),    # 32 channels, a 8-pixel last strip
+    (1, 34, 256, 64, 0, 64, 0),    # 64 channels, two chunks
+    (3, 17, 200, 32, 32, 64, 16),  # two tensors, odd rows, written into a 80-channel tensor's first 64
+])
+def test_conv_up2_matches_conv_then_upsample(pkg, n, h, w, c0, c1, cout, extra):
+    """glbm_nn_tc_conv_up2 (the streaming kernel writing its output 2x
+    nearest-upsampled by TMA stores) gives, bit for bit, the plain streaming
+    convolution followed by glbm_nn_upsample2_nhwc, and leaves the channels
+    beyond cout of a wider output tensor alone."""
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(n * 100 + h + cout)
+    cin = c0 + c1
+    nhwc = torch.from_numpy(rng.normal(size=(n, h, w, cin)).astype(np.float32)).to(torch.bfloat16).cuda()
+    x0 = nhwc[..., :c0].contiguous()
+    x1 = nhwc[..., c0:].contiguous() if c1 else None
+    wf = rng.normal(0.0, np.sqrt(2.0 / (cin * 9)), size=(cout, cin, 3, 3)).astype(np.float32)
+    wt = torch.empty(9 * cout * cin, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_tc_pack_weights(_vp(torch.from_numpy(wf.ravel()).cuda()), cout, cin, 3, cout, cin,
+                                       _vp(wt), _stream()) == 0
+    bdev = torch.from_numpy(rng.normal(0.0, 0.1, size=cout).astype(np.float32)).cuda()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    xp1 = _vp(x1) if x1 is not None else None
+    lib.glbm_nn_tc_set_variant(5)
+    try:
+        y = torch.empty((n, h, w, cout), dtype=torch.bfloat16, device="cuda")
+        assert lib.glbm_nn_tc_conv(_vp(x0), c0, xp1, c1, n, h, w, 3, _vp(wt), _vp(bdev), cout, _vp(y), cout, 1, 0, 0,
+                                   _vp(err), _stream()) == 0
+        ref = torch.empty((n, 2 * h, 2 * w, cout), dtype=torch.bfloat16, device="cuda")
+        assert lib.glbm_nn_upsample2_nhwc(_vp(y), n, cout, h, w, _vp(ref), _stream()) == 0
+        ys = cout + extra
+        up = torch.full((n, 2 * h, 2 * w, ys), float("nan"), dtype=torch.bfloat16, device="cuda")
+        rc = lib.glbm_nn_tc_conv_up2(_vp(x0), c0, xp1, c1, n, h, w, _vp(wt), _vp(bdev), cout, _vp(up), ys, 1,
+                                     _vp(err), _stream())
+    finally:
+        lib.glbm_nn_tc_set_variant(0)
+    assert rc == 0, lib.glbm_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert torch.equal(up[..., :cout], ref)
+    if extra:
+        assert torch.isnan(up[..., cout:].float()).all()
+
+
+def test_conv_up2_needs_the_streaming_kernel(pkg):
+    import torch
+    lib = pkg.load()
+    buf = torch.zeros(1 << 16, dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(32, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # rows of 64 pixels: no 128-pixel strip
+    assert lib.glbm_nn_tc_conv_up2(_vp(buf), 32, None, 0, 1, 8, 64, _vp(buf), _vp(b), 32, _vp(buf), 32, 1,
+                                   _vp(err), _stream()) == -1
+    assert b"streaming" in lib.glbm_last_error(None)
+    # 48 output channels
+    assert lib.glbm_nn_tc_conv_up2(_vp(buf), 32, None, 0, 1, 8, 256, _vp(buf), _vp(b), 48, _vp(buf), 48, 1,
+                                   _vp(err), _stream()) == -1
+
+
 def test_tc_conv_rejects_bad_shapes(pkg):
     import torch
     lib = pkg.load()
