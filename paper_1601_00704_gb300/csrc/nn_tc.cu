@@ -564,7 +564,10 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
 // With 64 output channels the ring has 8 slots of 64 columns and each input
 // row takes three N = 64 MMAs per tap and K step, one per output row (no
 // stacking, so no ring wrap inside an MMA); groups of two input rows leave
-// the epilogue two groups of slack in the 4 pair slots.
+// the epilogue two groups of slack in the 4 pair slots.  Where the weights
+// do not fit in shared memory (wstream), each stage brings the nine weight
+// tiles of its chunk along with its input rows (groups of four rows, so each
+// weight tile serves four rows per load).
 // Roles: warp 0 TMA (G input rows of one 32-channel chunk per stage: boxes
 // of G rows, as tall as the band kernel's, keep the TMA engine streaming),
 // warp 1 MMA and TMEM, warps 4-7 epilogue (one per lane quarter); every wait
@@ -596,6 +599,10 @@ struct StreamArgs {
     // mapY1: even / odd output columns) from a staged row pair; y unused
     int up2;
     uint32_t stage_y_bytes;  // one staged row: 128 pixels x COUT BF16
+    // 1: no resident weights; a stage = input rows (wofs bytes) + the nine
+    // weight tiles of its chunk
+    int wstream;
+    uint32_t wofs;
 };
 
 template <int G, int COUT>
@@ -609,7 +616,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int ntile_w = 9 * a.nchunk;
-    const int nslot_w = STACK ? 15 * a.nchunk + 2 : ntile_w;  // stacked: with their zero tiles
+    const int nslot_w = a.wstream ? 0 : (STACK ? 15 * a.nchunk + 2 : ntile_w);  // stacked: with zero tiles
     uint8_t *sW = smem;
     uint8_t *sA = smem + size_t(nslot_w) * a.wtile;
     // up2: two buffers of a staged row pair after the stages
@@ -674,12 +681,15 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
 
     if (warp == 0) {
         if (lane == 0) {
-            mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
-            for (int tap = 0; tap < 9; ++tap)
-                for (int ch = 0; ch < a.nchunk; ++ch)
-                    tma_load_3d(sW + size_t(STACK ? 2 + 5 * (ch * 3 + tap % 3) + (2 - tap / 3) : tap * a.nchunk + ch) *
-                                         a.wtile,
-                                &mapB, &wfull, ch * TC_KC, 0, tap);
+            if (!a.wstream) {
+                mbar_expect_tx(&wfull, uint32_t(ntile_w) * a.wtile);
+                for (int tap = 0; tap < 9; ++tap)
+                    for (int ch = 0; ch < a.nchunk; ++ch)
+                        tma_load_3d(
+                            sW + size_t(STACK ? 2 + 5 * (ch * 3 + tap % 3) + (2 - tap / 3) : tap * a.nchunk + ch) *
+                                     a.wtile,
+                            &mapB, &wfull, ch * TC_KC, 0, tap);
+            }
             long long i = 0;
             bool go = true;
             for (int g = 0; g < ngroups && go; ++g)
@@ -698,14 +708,17 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     for (int blk = 0; blk < a.nblk; ++blk)
                         tma_load_4d(dst + blk * a.blk_stride, first ? &mapA0 : &mapA1, &full[s], c0 + blk * 8,
                                     x0 - 1, ya - 1 + G * g, img);
+                    if (a.wstream)
+                        for (int tap = 0; tap < 9; ++tap)
+                            tma_load_3d(dst + a.wofs + size_t(tap) * a.wtile, &mapB, &full[s], ch * TC_KC, 0, tap);
                 }
-            mbar_drain(&wfull, 0);
+            if (!a.wstream) mbar_drain(&wfull, 0);
             drain_ring(full, S, i);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t id64 = idesc_bf16(64), id96 = idesc_bf16(96);
-            bool ok = mbar_wait(&wfull, 0, &abort_flag, a.err, 22);
+            bool ok = a.wstream || mbar_wait(&wfull, 0, &abort_flag, a.err, 22);
             tc_fence_after();
             const uint64_t zdesc = sdesc_nosw(smem_u32(szero), 2048u, 128u);
             const uint64_t wdesc = sdesc_k64(sW);
@@ -726,10 +739,10 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     }
                     tc_fence_after();
                     if (STACK) {
-                        umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, wdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, zdesc, id64, 0u);
                     } else {
-                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, wdesc, id64, 0u);
-                        umma_bf16(tmem + uint32_t((2 * ps + 1) * COUT), zdesc, wdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, zdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t((2 * ps + 1) * COUT), zdesc, zdesc, id64, 0u);
                     }
                 }
                 for (int ch = 0; ch < a.nchunk && ok; ++ch, ++i) {
@@ -741,7 +754,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     tc_fence_after();
                     const uint64_t a0 = sdesc_nosw(smem_u32(sA + size_t(s) * a.stage_bytes), a.blk_stride, 128u);
                     if (!STACK) {
-                        // input row G g + ri adds W(dy) to output row G g + ri + 1 - dy
+                        // input row G g + ri adds W(dy) to output row G g + ri + 1 - dy; the
+                        // weight tile of (tap, chunk) is resident or in this stage
+                        const uint64_t wbase = a.wstream ? sdesc_k64(sA + size_t(s) * a.stage_bytes + a.wofs) : wdesc;
 #pragma unroll 1
                         for (int ri = 0; ri < G; ++ri) {
                             const uint64_t arow = a0 + uint64_t(ri * BAND_PX);  // 16-byte units
@@ -750,7 +765,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                                 const uint32_t d = tmem + uint32_t(((G * g + ri + o) % NS) * COUT);
 #pragma unroll
                                 for (int dxi = 0; dxi < 3; ++dxi) {
-                                    const uint64_t bt = wdesc + uint64_t(((2 - o) * 3 + dxi) * a.nchunk + ch) * wt16;
+                                    const int tap = (2 - o) * 3 + dxi;
+                                    const uint64_t bt =
+                                        wbase + uint64_t(a.wstream ? tap : tap * a.nchunk + ch) * wt16;
 #pragma unroll
                                     for (int kk = 0; kk < 2; ++kk)
                                         if (kk < kks)
@@ -1230,16 +1247,25 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 // (image, 128-pixel strip, segment of L output rows), at most one CTA per SM;
 // false where the segments would be short (the band kernel's edge overhead
 // is then no worse) or the weights and two stages do not fit.
-bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, int *L, int *nseg, int *G, int *stages,
-                 size_t *smem, bool up2 = false) {
+struct StreamPlan {
+    int L, nseg, G, stages;
+    size_t smem;
+    bool wstream;        // weights travel with each stage (too many to keep resident)
+    uint32_t wofs;       // wstream: byte offset of the weight tiles in a stage
+    size_t stage_bytes;
+};
+
+bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, StreamPlan *p, bool up2 = false) {
     if (w < TC_M || g_tc_variant == 1 || g_tc_variant == 3 || g_tc_variant == 4) return false;
     if (cout != 32 && cout != 64) return false;
-    if (size_t(9) * kchunks(cin) * TC_KC * cout * 2 > kBandMaxWeights) return false;
-    // 32 output channels: the weight tiles with their zero tiles
-    // (with up2 also two staged row pairs: 2 x 2 x 128 pixels x cout BF16)
-    const size_t wbytes = (cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
-                                      : size_t(9) * kchunks(cin) * cout * TC_KC * 2) +
-                          (up2 ? size_t(4) * TC_M * cout * 2 : 0);
+    const bool resident = size_t(9) * kchunks(cin) * TC_KC * cout * 2 <= kBandMaxWeights;
+    // 32 output channels: resident weights only (the stacked tiles with
+    // their zero tiles); 64: resident, or nine tiles per stage
+    if (!resident && cout == 32) return false;
+    const size_t staged = up2 ? size_t(4) * TC_M * cout * 2 : 0;  // two staged row pairs
+    const size_t wbytes = !resident ? 0
+                          : cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
+                                       : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
     const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
@@ -1248,21 +1274,27 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, int *L, int *n
     int l = (h + segs - 1) / segs;
     l += l & 1;  // even: row pairs never straddle two segments
     if (l < (g_tc_variant == 5 ? 2 : 16)) return false;
-    *L = l;
-    *nseg = (h + l - 1) / l;
-    // the tallest group (6, 4 or 2 rows) that leaves three stages; with 64
-    // output channels two rows (the 4 pair slots need two groups of slack)
-    for (int g = cout == 32 ? 6 : 2; g >= 2; g -= 2) {
+    p->L = l;
+    p->nseg = (h + l - 1) / l;
+    p->wstream = !resident;
+    // the tallest group that leaves three stages: 6, 4 or 2 rows with 32
+    // output channels; 2 rows with 64 (the 4 pair slots need two groups of
+    // slack), 4 when each stage carries the weights (amortised over 4 rows)
+    const int g0 = cout == 32 ? 6 : (resident ? 2 : 4);
+    for (int g = g0; g >= 2; g -= 2) {
         const size_t blk = (size_t(g) * BAND_PX * 16 + 127) / 128 * 128;
-        const size_t stage = 4 * blk;
-        if (1024 + wbytes + 2 * stage > kStreamSmemLimit) continue;
-        const size_t room = kStreamSmemLimit - 1024 - wbytes;
+        const size_t arows = resident ? 4 * blk : (4 * blk + 1023) / 1024 * 1024;
+        const size_t stage = arows + (resident ? 0 : size_t(9) * cout * TC_KC * 2);
+        if (1024 + wbytes + staged + 2 * stage > kStreamSmemLimit) continue;
+        const size_t room = kStreamSmemLimit - 1024 - wbytes - staged;
         int st = int(room / stage);
         if (st > ST_SMAX) st = ST_SMAX;
         if (st < (g > 2 ? 3 : 2)) continue;
-        *G = g;
-        *stages = st;
-        *smem = 1024 + wbytes + size_t(st) * stage;
+        p->G = g;
+        p->stages = st;
+        p->wofs = uint32_t(arows);
+        p->stage_bytes = stage;
+        p->smem = 1024 + wbytes + staged + size_t(st) * stage;
         return true;
     }
     return false;
@@ -1270,9 +1302,11 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, int *L, int *n
 
 glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n, int h, int w, const CUtensorMap &mB,
                           const float *bias, int cout, void *y, long long ys, int relu, int *err, cudaStream_t st,
-                          int L, int nseg, int G, int stages, size_t smem, void *pool_y = nullptr,
-                          const void *head_w = nullptr, const float *head_b = nullptr, float *head_y = nullptr,
-                          int head_out = 0, bool up2 = false) {
+                          const StreamPlan &pl, void *pool_y = nullptr, const void *head_w = nullptr,
+                          const float *head_b = nullptr, float *head_y = nullptr, int head_out = 0,
+                          bool up2 = false) {
+    const int L = pl.L, nseg = pl.nseg, G = pl.G, stages = pl.stages;
+    const size_t smem = pl.smem;
     CUtensorMap mA0, mA1, mY0, mY1;
     if (up2) {
         // y (n, 2h, 2w, ys): output column 2j + e of full row r is element
@@ -1306,9 +1340,11 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.L = L;
     a.stages = stages;
     a.blk_stride = uint32_t((size_t(G) * BAND_PX * 16 + 127) / 128 * 128);
-    a.stage_bytes = 4 * a.blk_stride;
-    a.tx_bytes = uint32_t(a.nblk * G * BAND_PX * 16);
     a.wtile = uint32_t(cout * TC_KC * 2);
+    a.wstream = pl.wstream ? 1 : 0;
+    a.wofs = pl.wofs;
+    a.stage_bytes = uint32_t(pl.stage_bytes);
+    a.tx_bytes = uint32_t(a.nblk * G * BAND_PX * 16) + (pl.wstream ? 9 * a.wtile : 0u);
     a.bias = bias;
     a.y = y;
     a.ys = ys;
@@ -1326,7 +1362,7 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
         mY0 = mA0;  // unused
         mY1 = mA0;
     }
-    const auto kern = cout == 64 ? k_tc_conv_stream<2, 64>
+    const auto kern = cout == 64 ? (G == 4 ? k_tc_conv_stream<4, 64> : k_tc_conv_stream<2, 64>)
                                  : (G == 6 ? k_tc_conv_stream<6, 32>
                                            : (G == 4 ? k_tc_conv_stream<4, 32> : k_tc_conv_stream<2, 32>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1392,12 +1428,13 @@ extern "C" glbm_status glbm_nn_tc_conv(const void *x0, int c0, const void *x1, i
     }
     int nsm = 0;
     if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv: device query failed");
-    int R = 0, stages = 0, L = 0, nseg = 0, G = 0;
+    int R = 0, stages = 0;
     size_t bsmem = 0;
     int stack = 0;
-    if (k == 3 && !f32_nchw && stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &bsmem))
+    StreamPlan pl;
+    if (k == 3 && !f32_nchw && stream_plan(w, h, n, cin, cout, nsm, &pl))
         return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
-                             static_cast<cudaStream_t>(stream), L, nseg, G, stages, bsmem);
+                             static_cast<cudaStream_t>(stream), pl);
     if (g_tc_variant != 1 && band_plan(k, f32_nchw, w, cin, cout, h, &R, &stages, &bsmem, &stack))
         return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
                            static_cast<cudaStream_t>(stream), R, stages, bsmem, stack);
@@ -1457,10 +1494,11 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
     if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: arrays must be 16-byte aligned");
     if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: cuTensorMapEncodeTiled is not available");
     const int cin = c0 + c1;
-    int R = 0, stages = 0, stack = 0, nsm = 0, L = 0, nseg = 0, G = 0;
+    int R = 0, stages = 0, stack = 0, nsm = 0;
     size_t smem = 0;
     if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv_fused: device query failed");
-    const bool streaming = stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &smem);
+    StreamPlan pl;
+    const bool streaming = stream_plan(w, h, n, cin, cout, nsm, &pl);
     if (!streaming && (!band_plan(3, 0, w, cin, cout, h, &R, &stages, &smem, &stack) || (cout == 32 && !stack)))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_fused: the layer does not fit the band kernel");
     if (!streaming && pool_y && R % 2) --R;  // pooling pairs the rows of a band (fewer rows need less memory)
@@ -1479,8 +1517,7 @@ extern "C" glbm_status glbm_nn_tc_conv_fused(const void *x0, int c0, const void 
     }
     if (streaming)
         return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err,
-                             static_cast<cudaStream_t>(stream), L, nseg, G, stages, smem, pool_y, head_w, head_b,
-                             head_y, head_out);
+                             static_cast<cudaStream_t>(stream), pl, pool_y, head_w, head_b, head_y, head_out);
     return launch_band(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
                        R, stages, smem, stack, pool_y, head_w, head_b, head_y, head_out);
 }
@@ -1498,10 +1535,10 @@ extern "C" glbm_status glbm_nn_tc_conv_up2(const void *x0, int c0, const void *x
     if (mis) return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: arrays must be 16-byte aligned");
     if (!encode_fn()) return tcfail(GLBM_ECUDA, "nn_tc_conv_up2: cuTensorMapEncodeTiled is not available");
     const int cin = c0 + c1;
-    int nsm = 0, L = 0, nseg = 0, G = 0, stages = 0;
-    size_t smem = 0;
+    int nsm = 0;
     if (sm_count(&nsm)) return tcfail(GLBM_ECUDA, "nn_tc_conv_up2: device query failed");
-    if (!stream_plan(w, h, n, cin, cout, nsm, &L, &nseg, &G, &stages, &smem, true))
+    StreamPlan pl;
+    if (!stream_plan(w, h, n, cin, cout, nsm, &pl, true))
         return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: the layer does not fit the streaming kernel");
     CUtensorMap mB;
     {
@@ -1515,7 +1552,7 @@ extern "C" glbm_status glbm_nn_tc_conv_up2(const void *x0, int c0, const void *x
             return tcfail(GLBM_EINVAL, "nn_tc_conv_up2: weight tensor map rejected");
     }
     return launch_stream(x0, c0, x1, c1, n, h, w, mB, bias, cout, y, ys, relu, err, static_cast<cudaStream_t>(stream),
-                         L, nseg, G, stages, smem, nullptr, nullptr, nullptr, nullptr, 0, true);
+                         pl, nullptr, nullptr, nullptr, nullptr, 0, true);
 }
 
 extern "C" glbm_status glbm_nn_tc_pack_weights(const float *wf, int cout, int cin, int k, int cout_pad,

@@ -58,6 +58,7 @@ CASES = [
     (2, 20, 40, 16, 0, 32, 3, True, False),     # tile kernel
     (1, 24, 256, 16, 0, 32, 3, True, False),    # band / streaming
     (1, 12, 300, 16, 0, 64, 3, True, False),    # band, 64 output channels
+    (1, 12, 256, 128, 64, 64, 3, True, False),  # 221 KB of weights: tile kernel, or streaming with the weights in each stage
 ]
 
 
@@ -166,10 +167,13 @@ def _band_layer(pkg, rng, n, h, w, c0, c1, variant, fused, cout=32):
     (150, 40, 128, 32, 0, True, 64),    # 64 output channels: the 8-slot ring wrapped five times, fused pooling
     (76, 33, 200, 64, 0, False, 64),    # two chunks, odd rows, ragged last strip
     (1, 300, 1024, 32, 32, True, 64),   # two tensors, 8 strips x 19 segments
+    (76, 33, 200, 128, 64, False, 64),  # weights too large to keep: each stage brings its chunk's 9 tiles
+    (1, 300, 1024, 96, 0, False, 64),   # the same, one tensor of 3 chunks, 8 strips x 19 segments
 ])
 def test_streaming_conv_matches_band_kernel(pkg, n, h, w, c0, c1, fused, cout):
     """The streaming form (variant 5) against the band kernel (variant 4,
-    stacked for 32 output channels), on layers whose segments wrap the TMEM
+    stacked for 32 output channels; the tile kernel where the weights exceed
+    the band kernel's 80 KB), on layers whose segments wrap the TMEM
     row ring: the same products of the same BF16 values, summed in the same
     order for one 32-channel chunk and in another chunk order for two or
     three, so outputs agree to at most one BF16 ulp (exactly for one chunk,
