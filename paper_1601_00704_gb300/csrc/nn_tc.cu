@@ -561,10 +561,13 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
 // so that each adds only its part.  The weights of one (chunk, dx) sit as
 // [0 0 W(+1) W(0) W(-1) 0 0] in shared memory, neighbours sharing their
 // zero tiles.
-// With 64 output channels the ring has 8 slots of 64 columns and each input
-// row takes three N = 64 MMAs per tap and K step, one per output row (no
-// stacking, so no ring wrap inside an MMA); groups of two input rows leave
-// the epilogue two groups of slack in the 4 pair slots.  Where the weights
+// With 64 output channels the ring has 8 slots of 64 columns.  Where the
+// stacked weights with their zero tiles fit in shared memory (STK), each
+// input row takes one N = 192 MMA per tap and K step as above; otherwise
+// three N = 64 MMAs, one per output row (no stacking, so no ring wrap inside
+// an MMA).  A single thread issues MMAs no faster than about one per 46
+// cycles whatever their size, so fewer, larger MMAs win.  Groups of two
+// input rows leave the epilogue two groups of slack in the 4 pair slots.  Where the weights
 // do not fit in shared memory (wstream), each stage brings the nine weight
 // tiles of its chunk along with its input rows (groups of four rows, so each
 // weight tile serves four rows per load).
@@ -605,12 +608,12 @@ struct StreamArgs {
     uint32_t wofs;
 };
 
-template <int G, int COUT>
+template <int G, int COUT, bool STK>
 __global__ void __launch_bounds__(ST_THREADS, 1)
 k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constant__ CUtensorMap mapA1,
                  const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapY0,
                  const __grid_constant__ CUtensorMap mapY1, const StreamArgs a) {
-    constexpr bool STACK = COUT == 32;  // dy taps stacked along N
+    constexpr bool STACK = STK;  // dy taps stacked along N (N = 3 COUT)
     constexpr int NS = 512 / COUT;      // TMEM row slots
     constexpr int NP = NS / 2;          // row pair slots
     extern __shared__ uint8_t smem_raw[];
@@ -717,14 +720,16 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id64 = idesc_bf16(64), id96 = idesc_bf16(96);
+            // MMA shapes: the main N (3 COUT stacked, else COUT) and the clearing
+            // of a row pair's two slots
+            const uint32_t idN = idesc_bf16(STACK ? 3 * COUT : COUT), idZ = idesc_bf16(STACK ? 2 * COUT : COUT);
             bool ok = a.wstream || mbar_wait(&wfull, 0, &abort_flag, a.err, 22);
             tc_fence_after();
             const uint64_t zdesc = sdesc_nosw(smem_u32(szero), 2048u, 128u);
             const uint64_t wdesc = sdesc_k64(sW);
             const uint32_t wt16 = a.wtile >> 4, kstep = (2 * a.blk_stride) >> 4;
             const int kks = a.nblk / 2;  // K steps of 16 channels per chunk
-            const uint32_t d13 = uint32_t((NS - 3) * 32);
+            const uint32_t d13 = uint32_t((NS - 3) * COUT);
             long long i = 0;
             for (int g = 0; g < ngroups && ok; ++g) {
                 // pairs hg g + 1 .. hg g + hg enter their slots: wait until the
@@ -739,10 +744,10 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                     }
                     tc_fence_after();
                     if (STACK) {
-                        umma_bf16(tmem + uint32_t(2 * ps * 32), zdesc, zdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, zdesc, idZ, 0u);
                     } else {
-                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, zdesc, id64, 0u);
-                        umma_bf16(tmem + uint32_t((2 * ps + 1) * COUT), zdesc, zdesc, id64, 0u);
+                        umma_bf16(tmem + uint32_t(2 * ps * COUT), zdesc, zdesc, idZ, 0u);
+                        umma_bf16(tmem + uint32_t((2 * ps + 1) * COUT), zdesc, zdesc, idZ, 0u);
                     }
                 }
                 for (int ch = 0; ch < a.nchunk && ok; ++ch, ++i) {
@@ -772,7 +777,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                                     for (int kk = 0; kk < 2; ++kk)
                                         if (kk < kks)
                                             umma_bf16(d, arow + uint64_t(dxi + kk * kstep), bt + uint64_t(kk * 2),
-                                                      id64, 1u);
+                                                      idN, 1u);
                                 }
                             }
                         }
@@ -787,14 +792,14 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                         const int s0 = (G * g + ri) % NS;
                         const uint64_t arow = a0 + uint64_t(ri * BAND_PX);  // 16-byte units
                         if (s0 <= NS - 3) {
-                            const uint32_t d0 = tmem + uint32_t(s0 * 32);
+                            const uint32_t d0 = tmem + uint32_t(s0 * COUT);
 #pragma unroll
                             for (int dxi = 0; dxi < 3; ++dxi)
 #pragma unroll
                                 for (int kk = 0; kk < 2; ++kk)
                                     if (kk < kks)
                                         umma_bf16(d0, arow + uint64_t(dxi + kk * kstep),
-                                                  b0 + uint64_t(5 * dxi * wt16 + kk * 2), id96, 1u);
+                                                  b0 + uint64_t(5 * dxi * wt16 + kk * 2), idN, 1u);
                         } else {
                             // slots 13-15 take B shifted by 1 (s0 = 14: [0 W(+1) W(0)]) or
                             // 2 (s0 = 15: [0 0 W(+1)]) tiles; slots 0-2 the rest, shifted
@@ -807,8 +812,8 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                                     if (kk >= kks) break;
                                     const uint64_t ad = arow + uint64_t(dxi + kk * kstep);
                                     const uint64_t bk = b0 + uint64_t(5 * dxi * wt16 + kk * 2);
-                                    umma_bf16(tmem + d13, ad, bk - uint64_t(sh * wt16), id96, 1u);
-                                    umma_bf16(tmem, ad, bk + uint64_t((3 - sh) * wt16), id96, 1u);
+                                    umma_bf16(tmem + d13, ad, bk - uint64_t(sh * wt16), idN, 1u);
+                                    umma_bf16(tmem, ad, bk + uint64_t((3 - sh) * wt16), idN, 1u);
                                 }
                         }
                     }
@@ -1249,6 +1254,7 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 // is then no worse) or the weights and two stages do not fit.
 struct StreamPlan {
     int L, nseg, G, stages;
+    bool stack;          // dy taps stacked along N (resident weights with zero tiles)
     size_t smem;
     bool wstream;        // weights travel with each stage (too many to keep resident)
     uint32_t wofs;       // wstream: byte offset of the weight tiles in a stage
@@ -1263,9 +1269,12 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, StreamPlan *p,
     // their zero tiles); 64: resident, or nine tiles per stage
     if (!resident && cout == 32) return false;
     const size_t staged = up2 ? size_t(4) * TC_M * cout * 2 : 0;  // two staged row pairs
-    const size_t wbytes = !resident ? 0
-                          : cout == 32 ? size_t(15 * kchunks(cin) + 2) * 32 * TC_KC * 2
-                                       : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
+    // stacked tiles with their zero tiles; 64 output channels stack where
+    // those fit with two stages of two rows, else the plain tiles
+    const size_t wstack = size_t(15 * kchunks(cin) + 2) * cout * TC_KC * 2;
+    const size_t stage2 = 4 * ((size_t(2) * BAND_PX * 16 + 127) / 128 * 128);
+    const bool stack = resident && (cout == 32 || 1024 + wstack + staged + 2 * stage2 <= 221 * 1024);
+    const size_t wbytes = !resident ? 0 : stack ? wstack : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
     const long long units = (long long)n * ((w + TC_M - 1) / TC_M);
@@ -1277,6 +1286,7 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, StreamPlan *p,
     p->L = l;
     p->nseg = (h + l - 1) / l;
     p->wstream = !resident;
+    p->stack = stack;
     // the tallest group that leaves three stages: 6, 4 or 2 rows with 32
     // output channels; 2 rows with 64 (the 4 pair slots need two groups of
     // slack), 4 when each stage carries the weights (amortised over 4 rows)
@@ -1362,9 +1372,11 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
         mY0 = mA0;  // unused
         mY1 = mA0;
     }
-    const auto kern = cout == 64 ? (G == 4 ? k_tc_conv_stream<4, 64> : k_tc_conv_stream<2, 64>)
-                                 : (G == 6 ? k_tc_conv_stream<6, 32>
-                                           : (G == 4 ? k_tc_conv_stream<4, 32> : k_tc_conv_stream<2, 32>));
+    const auto kern =
+        cout == 64 ? (pl.stack ? k_tc_conv_stream<2, 64, true>
+                               : (G == 4 ? k_tc_conv_stream<4, 64, false> : k_tc_conv_stream<2, 64, false>))
+                   : (G == 6 ? k_tc_conv_stream<6, 32, true>
+                             : (G == 4 ? k_tc_conv_stream<4, 32, true> : k_tc_conv_stream<2, 32, true>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return tccuda(e, "nn_tc_conv: shared memory attribute (streaming)");
     const unsigned grid = unsigned((long long)n * a.nbx * nseg);
