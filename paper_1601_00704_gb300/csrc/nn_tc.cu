@@ -601,6 +601,7 @@ struct StreamArgs {
     // 1: the output goes 2x nearest-upsampled to y by TMA stores (mapY0 /
     // mapY1: even / odd output columns) from a staged row pair; y unused
     int up2;
+    int ystages;             // staged row pairs: 2 (double buffered) or 1
     uint32_t stage_y_bytes;  // one staged row: 128 pixels x COUT BF16
     // 1: no resident weights; a stage = input rows (wofs bytes) + the nine
     // weight tiles of its chunk
@@ -652,11 +653,16 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     if (a.head_y && threadIdx.x < a.head_out) shead_b[threadIdx.x] = a.head_b[threadIdx.x];
     for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
     if (STACK) {
-        // the zero tiles: 0, 1 and 5 + 5k, 6 + 5k around (chunk, dx) group k
+        // the zero tiles: 0, 1 and 5 + 5k, 6 + 5k around (chunk, dx) group k,
+        // in the resident weights or, with wstream, in every stage's 17 tiles
         const int per = int(a.wtile / 16);
-        for (int j = threadIdx.x; j < nslot_w * per; j += blockDim.x) {
-            const int t = j / per;
-            if (t < 2 || (t - 2) % 5 >= 3) reinterpret_cast<uint4 *>(sW)[j] = make_uint4(0, 0, 0, 0);
+        const int nw = a.wstream ? 17 : nslot_w;
+        for (int st = 0; st < (a.wstream ? a.stages : 1); ++st) {
+            uint4 *wz = reinterpret_cast<uint4 *>(a.wstream ? sA + size_t(st) * a.stage_bytes + a.wofs : sW);
+            for (int j = threadIdx.x; j < nw * per; j += blockDim.x) {
+                const int t = j / per;
+                if (t < 2 || (t - 2) % 5 >= 3) wz[j] = make_uint4(0, 0, 0, 0);
+            }
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -713,7 +719,9 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                                     x0 - 1, ya - 1 + G * g, img);
                     if (a.wstream)
                         for (int tap = 0; tap < 9; ++tap)
-                            tma_load_3d(dst + a.wofs + size_t(tap) * a.wtile, &mapB, &full[s], ch * TC_KC, 0, tap);
+                            tma_load_3d(dst + a.wofs +
+                                            size_t(STACK ? 2 + 5 * (tap % 3) + (2 - tap / 3) : tap) * a.wtile,
+                                        &mapB, &full[s], ch * TC_KC, 0, tap);
                 }
             if (!a.wstream) mbar_drain(&wfull, 0);
             drain_ring(full, S, i);
@@ -784,8 +792,11 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                         umma_commit(&empty[s]);
                         continue;
                     }
-                    // B of (chunk, dx) group k starts at tile 2 + 5k: [W(+1) W(0) W(-1)]
-                    const uint64_t b0 = sdesc_k64(sW) + uint64_t((2 + 15 * ch) * wt16);
+                    // B of (chunk, dx) group k starts at tile 2 + 5k: [W(+1) W(0) W(-1)];
+                    // with wstream the stage holds this chunk's 17 tiles
+                    const uint64_t b0 = a.wstream
+                                            ? sdesc_k64(sA + size_t(s) * a.stage_bytes + a.wofs) + uint64_t(2 * wt16)
+                                            : sdesc_k64(sW) + uint64_t((2 + 15 * ch) * wt16);
 #pragma unroll 1
                     for (int ri = 0; ri < G; ++ri) {
                         // input row G g + ri feeds the slots of rows G g + ri .. + 2
@@ -834,13 +845,19 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
         for (int P = 1; P <= npairs; ++P) {
             const int ps = P % NP;
             const bool got = mbar_wait_idle(&pfull[ps], uint32_t((P - 1) / NP) & 1u, &abort_flag, a.err, 25);
-            uint8_t *stg = sY + size_t(P & 1) * 2 * a.stage_y_bytes;
+            uint8_t *stg = sY + size_t(a.ystages == 2 ? (P & 1) : 0) * 2 * a.stage_y_bytes;
             if (a.up2) {
                 // the four warps agree before the named barriers below, so that a
                 // wait that gave up can never leave a warp waiting at one of them
                 if (!got) s_bad = 1;
-                // the stores issued two pairs ago from this buffer have read it
-                if (warp == 4 && lane == 0) bulk_wait_read1();
+                // the stores issued from this buffer (two pairs ago, or the last
+                // pair's with one buffer) have read it
+                if (warp == 4 && lane == 0) {
+                    if (a.ystages == 2)
+                        bulk_wait_read1();
+                    else
+                        bulk_wait_read0();
+                }
                 asm volatile("bar.sync 1, 128;" ::: "memory");
                 const int bad = s_bad;
                 asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -1254,7 +1271,8 @@ glbm_status launch_band(const void *x0, int c0, const void *x1, int c1, int n, i
 // is then no worse) or the weights and two stages do not fit.
 struct StreamPlan {
     int L, nseg, G, stages;
-    bool stack;          // dy taps stacked along N (resident weights with zero tiles)
+    bool stack;          // dy taps stacked along N (weights with zero tiles)
+    int ystages;         // up2: staged row pairs (2, or 1 where two do not fit)
     size_t smem;
     bool wstream;        // weights travel with each stage (too many to keep resident)
     uint32_t wofs;       // wstream: byte offset of the weight tiles in a stage
@@ -1268,12 +1286,18 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, StreamPlan *p,
     // 32 output channels: resident weights only (the stacked tiles with
     // their zero tiles); 64: resident, or nine tiles per stage
     if (!resident && cout == 32) return false;
-    const size_t staged = up2 ? size_t(4) * TC_M * cout * 2 : 0;  // two staged row pairs
     // stacked tiles with their zero tiles; 64 output channels stack where
-    // those fit with two stages of two rows, else the plain tiles
+    // those fit with two stages of two rows (and with up2 two staged row
+    // pairs: a single staging buffer serialises the stores with the
+    // epilogue and cost more than stacking saved, d1b 116 -> 133 us), else
+    // the plain tiles; weights carried in each stage stack too (17 tiles per
+    // stage)
     const size_t wstack = size_t(15 * kchunks(cin) + 2) * cout * TC_KC * 2;
     const size_t stage2 = 4 * ((size_t(2) * BAND_PX * 16 + 127) / 128 * 128);
-    const bool stack = resident && (cout == 32 || 1024 + wstack + staged + 2 * stage2 <= 221 * 1024);
+    const size_t pair_y = size_t(2) * TC_M * cout * 2;
+    const int ystages = up2 ? 2 : 0;
+    const bool stack = cout == 32 || !resident || 1024 + wstack + ystages * pair_y + 2 * stage2 <= 221 * 1024;
+    const size_t staged = size_t(ystages) * pair_y;
     const size_t wbytes = !resident ? 0 : stack ? wstack : size_t(9) * kchunks(cin) * cout * TC_KC * 2;
     // the 227 KB per block less this kernel's ~5 KB of static shared memory
     constexpr size_t kStreamSmemLimit = 221 * 1024;
@@ -1287,14 +1311,15 @@ bool stream_plan(int w, int h, int n, int cin, int cout, int nsm, StreamPlan *p,
     p->nseg = (h + l - 1) / l;
     p->wstream = !resident;
     p->stack = stack;
+    p->ystages = ystages;
     // the tallest group that leaves three stages: 6, 4 or 2 rows with 32
     // output channels; 2 rows with 64 (the 4 pair slots need two groups of
     // slack), 4 when each stage carries the weights (amortised over 4 rows)
-    const int g0 = cout == 32 ? 6 : (resident ? 2 : 4);
+    const int g0 = cout == 32 ? 6 : (resident || stack ? 2 : 4);
     for (int g = g0; g >= 2; g -= 2) {
         const size_t blk = (size_t(g) * BAND_PX * 16 + 127) / 128 * 128;
         const size_t arows = resident ? 4 * blk : (4 * blk + 1023) / 1024 * 1024;
-        const size_t stage = arows + (resident ? 0 : size_t(9) * cout * TC_KC * 2);
+        const size_t stage = arows + (resident ? 0 : size_t(stack ? 17 : 9) * cout * TC_KC * 2);
         if (1024 + wbytes + staged + 2 * stage > kStreamSmemLimit) continue;
         const size_t room = kStreamSmemLimit - 1024 - wbytes - staged;
         int st = int(room / stage);
@@ -1366,6 +1391,7 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
     a.head_y = head_y;
     a.head_out = head_out;
     a.up2 = up2 ? 1 : 0;
+    a.ystages = pl.ystages;
     a.stage_y_bytes = uint32_t(TC_M * cout * 2);
     if (up2) a.y = nullptr;
     if (!up2) {
@@ -1373,7 +1399,7 @@ glbm_status launch_stream(const void *x0, int c0, const void *x1, int c1, int n,
         mY1 = mA0;
     }
     const auto kern =
-        cout == 64 ? (pl.stack ? k_tc_conv_stream<2, 64, true>
+        cout == 64 ? (pl.stack ? (G == 4 ? k_tc_conv_stream<4, 64, true> : k_tc_conv_stream<2, 64, true>)
                                : (G == 4 ? k_tc_conv_stream<4, 64, false> : k_tc_conv_stream<2, 64, false>))
                    : (G == 6 ? k_tc_conv_stream<6, 32, true>
                              : (G == 4 ? k_tc_conv_stream<4, 32, true> : k_tc_conv_stream<2, 32, true>));
