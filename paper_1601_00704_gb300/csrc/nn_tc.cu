@@ -630,7 +630,8 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ __align__(16) float sbias[COUT];
-    __shared__ float shead[4 * 32], shead_b[4];
+    __shared__ __align__(16) float shead[4 * 32];
+    __shared__ float shead_b[4];
     __shared__ __align__(128) uint8_t szero[4096];  // all-zero A (128 rows x 16 K, unswizzled)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -649,7 +650,10 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
     const int ngroups = (Lseg + 2 + G - 1) / G;
     const int npairs = (Lseg + 1) / 2;
     if (threadIdx.x < COUT) sbias[threadIdx.x] = a.bias[threadIdx.x];
-    if (a.head_y && threadIdx.x < a.head_out * 32) shead[threadIdx.x] = __bfloat162float(a.head_w[threadIdx.x]);
+    // head weights, zero for the outputs beyond head_out (computed, never stored)
+    if (threadIdx.x < 4 * 32)
+        shead[threadIdx.x] =
+            a.head_y && threadIdx.x < a.head_out * 32 ? __bfloat162float(a.head_w[threadIdx.x]) : 0.0f;
     if (a.head_y && threadIdx.x < a.head_out) shead_b[threadIdx.x] = a.head_b[threadIdx.x];
     for (int j = threadIdx.x; j < 4096 / 16; j += blockDim.x) reinterpret_cast<uint4 *>(szero)[j] = make_uint4(0, 0, 0, 0);
     if (STACK) {
@@ -914,7 +918,7 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                             dst[j4] = make_uint4(pk[u][4 * j4], pk[u][4 * j4 + 1], pk[u][4 * j4 + 2], pk[u][4 * j4 + 3]);
                     }
                 }
-                if (a.pool_y || (STACK && a.head_y)) {
+                if (a.pool_y || (COUT == 32 && a.head_y)) {
                     // the fused outputs start from the BF16-rounded values
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
@@ -925,18 +929,29 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                             v[u][2 * j + 1] = f.y;
                         }
                 }
-                if (STACK && a.head_y) {
+                if (COUT == 32 && a.head_y) {
+                    // all (up to 4) head outputs in one pass: four independent FMA
+                    // chains, each in channel order, weights read as float4
+                    const float4 *sh4 = reinterpret_cast<const float4 *>(shead);
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         if (r0 + u >= Lseg) break;
-                        for (int k = 0; k < a.head_out; ++k) {
-                            float acc_h = 0.0f;
+                        float acc_h[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                            for (int cc = 0; cc < 32; ++cc) acc_h = fmaf(v[u][cc], shead[k * 32 + cc], acc_h);
-                            if (colok)
-                                a.head_y[(((long long)img * a.head_out + k) * a.h + ya + r0 + u) * a.w + px] =
-                                    acc_h + shead_b[k];
-                        }
+                        for (int j4 = 0; j4 < 8; ++j4)
+#pragma unroll
+                            for (int kh = 0; kh < 4; ++kh) {
+                                const float4 wv = sh4[kh * 8 + j4];
+                                acc_h[kh] = fmaf(v[u][4 * j4], wv.x, acc_h[kh]);
+                                acc_h[kh] = fmaf(v[u][4 * j4 + 1], wv.y, acc_h[kh]);
+                                acc_h[kh] = fmaf(v[u][4 * j4 + 2], wv.z, acc_h[kh]);
+                                acc_h[kh] = fmaf(v[u][4 * j4 + 3], wv.w, acc_h[kh]);
+                            }
+#pragma unroll
+                        for (int kh = 0; kh < 4; ++kh)
+                            if (kh < a.head_out && colok)
+                                a.head_y[(((long long)img * a.head_out + kh) * a.h + ya + r0 + u) * a.w + px] =
+                                    acc_h[kh] + shead_b[kh];
                     }
                 }
                 if (a.pool_y) {
