@@ -956,29 +956,38 @@ k_tc_conv_stream(const __grid_constant__ CUtensorMap mapA0, const __grid_constan
                 }
                 if (a.pool_y) {
                     // rows r0, r0 + 1 (ya and r0 even) and pixels px, px ^ 1 (lanes
-                    // lane, lane ^ 1): FP32 ((a + b) + (d + e)) / 4, rounded to BF16
-                    const bool wr = (lane & 1) == 0 && colok && r0 + 1 < Lseg;
-                    uint32_t pp[16];
+                    // lane, lane ^ 1): the even lane pools channels 0-15 and the odd
+                    // one 16-31, each receiving that half of the other pixel (16
+                    // shuffles per row instead of 32); FP32 ((a + b) + (d + e)) / 4,
+                    // rounded to BF16 (addition commutes: the same bits whichever
+                    // lane adds)
+                    const int odd = lane & 1;
+                    const bool wr = colok && r0 + 1 < Lseg;
+                    uint32_t pp[8];
 #pragma unroll
-                    for (int cc = 0; cc < 32; cc += 2) {
+                    for (int cj = 0; cj < 16; cj += 2) {
                         float s2[2];
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
-                            const float mine_top = v[0][cc + e], mine_bot = v[1][cc + e];
-                            const float nb_top = __shfl_xor_sync(0xffffffffu, mine_top, 1);
-                            const float nb_bot = __shfl_xor_sync(0xffffffffu, mine_bot, 1);
+                            const int c = cj + e;
+                            const float mine_top = odd ? v[0][16 + c] : v[0][c];
+                            const float mine_bot = odd ? v[1][16 + c] : v[1][c];
+                            const float give_top = odd ? v[0][c] : v[0][16 + c];
+                            const float give_bot = odd ? v[1][c] : v[1][16 + c];
+                            const float nb_top = __shfl_xor_sync(0xffffffffu, give_top, 1);
+                            const float nb_bot = __shfl_xor_sync(0xffffffffu, give_bot, 1);
                             s2[e] = 0.25f * ((mine_top + nb_top) + (mine_bot + nb_bot));
                         }
                         __nv_bfloat162 b2 = __floats2bfloat162_rn(s2[0], s2[1]);
-                        pp[cc / 2] = *reinterpret_cast<uint32_t *>(&b2);
+                        pp[cj / 2] = *reinterpret_cast<uint32_t *>(&b2);
                     }
                     if (wr) {
                         const int pyo = (ya + r0) >> 1;
                         uint4 *dst = reinterpret_cast<uint4 *>(
-                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * COUT + cg * 32);
-#pragma unroll
-                        for (int j4 = 0; j4 < 4; ++j4)
-                            dst[j4] = make_uint4(pp[4 * j4], pp[4 * j4 + 1], pp[4 * j4 + 2], pp[4 * j4 + 3]);
+                            a.pool_y + (((long long)img * (a.h >> 1) + pyo) * (a.w >> 1) + (px >> 1)) * COUT + cg * 32 +
+                            odd * 16);
+                        dst[0] = make_uint4(pp[0], pp[1], pp[2], pp[3]);
+                        dst[1] = make_uint4(pp[4], pp[5], pp[6], pp[7]);
                     }
                 }
             }
