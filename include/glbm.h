@@ -544,19 +544,22 @@ void glbm_nn_tc_debug_starve(int stage);
 /* Choice of tensor-core convolution kernel for glbm_nn_tc_conv and
  * glbm_nn_tc_conv_fused (process-wide):
  * 0 (default) = per layer: 3x3 layers with BF16 output, rows of >= 128
- * pixels and 32 or 64 output channels whose weights fit shared memory run the
- * band kernel (weights resident, each band's halo loaded once per 32-channel
- * chunk; with 32 output channels the three vertical taps are stacked into
- * one MMA of 96 columns), and those with 32 output channels where one CTA
- * per (image, 128-pixel strip) leaves segments of >= 16 rows per SM run its
- * streaming form (each CTA walks down its strip, each input row multiplied
- * once into a ring of row accumulators); the rest run the tile kernel (one
- * 128-pixel tile per CTA, one TMA tile per tap; a 3-stage TMA ring, or an
- * 8-stage one when the grid has at most one CTA per SM); 1 = tile kernel
- * always; 2 = as 0 but the tile kernel always with the 3-stage ring; 3 =
- * band kernel where it applies but never stacked or streaming; 4 = band
- * kernel, stacked, never streaming; 5 = as 0 with streaming however short
- * its segments.  All compute the same convolution; other values reset to 0. */
+ * pixels and 32 or 64 output channels where one CTA per (image, 128-pixel
+ * strip) leaves segments of >= 16 rows per SM run the streaming kernel (each
+ * CTA walks down its strip, each input row multiplied once into a ring of
+ * row accumulators in tensor memory; the three vertical taps stacked into
+ * one MMA of 96 or 192 columns where the weights fit shared memory with
+ * their zero tiles; 64-channel layers whose weights exceed it take them
+ * along with each stage); other such layers whose weights fit shared memory
+ * run the band kernel (weights resident, each band's halo loaded once per
+ * 32-channel chunk; stacked taps for 32 output channels); the rest run the
+ * tile kernel (one 128-pixel tile per CTA, one TMA tile per tap; a 3-stage
+ * TMA ring, or an 8-stage one when the grid has at most one CTA per SM);
+ * 1 = tile kernel always; 2 = as 0 but the tile kernel always with the
+ * 3-stage ring; 3 = band kernel where it applies but never stacked or
+ * streaming; 4 = band kernel, stacked, never streaming; 5 = as 0 with
+ * streaming however short its segments.  All compute the same convolution;
+ * other values reset to 0. */
 void glbm_nn_tc_set_variant(int variant);
 
 /* FP32 [cout][cin][ksize][ksize] -> BF16 [ksize^2][cout_pad][cin_pad] (the

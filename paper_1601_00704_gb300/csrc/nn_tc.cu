@@ -567,10 +567,12 @@ k_tc_conv_band(const __grid_constant__ CUtensorMap mapA0, const __grid_constant_
 // three N = 64 MMAs, one per output row (no stacking, so no ring wrap inside
 // an MMA).  A single thread issues MMAs no faster than about one per 46
 // cycles whatever their size, so fewer, larger MMAs win.  Groups of two
-// input rows leave the epilogue two groups of slack in the 4 pair slots.  Where the weights
-// do not fit in shared memory (wstream), each stage brings the nine weight
-// tiles of its chunk along with its input rows (groups of four rows, so each
-// weight tile serves four rows per load).
+// input rows leave the epilogue two groups of slack in the 4 pair slots.
+// Where the weights do not fit in shared memory (wstream), each stage brings
+// the nine weight tiles of its chunk along with its input rows (stacked: in
+// the 17-tile layout with its zero tiles; else four-row groups, so that each
+// weight tile serves four rows per load).  With up2 the epilogue writes the
+// output 2x nearest-upsampled by TMA stores from a staged row pair.
 // Roles: warp 0 TMA (G input rows of one 32-channel chunk per stage: boxes
 // of G rows, as tall as the band kernel's, keep the TMA engine streaming),
 // warp 1 MMA and TMEM, warps 4-7 epilogue (one per lane quarter); every wait
