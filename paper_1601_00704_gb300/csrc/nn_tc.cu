@@ -37,6 +37,12 @@
 #include "tc_common.cuh"
 
 __attribute__((visibility("hidden"))) int g_tc_starve = 0;
+// 0 = choose per layer, 1 = tile kernel only (and the per-tap weight
+// gradient), 2 = as 0 with the tile kernel's ring never deepened, 3 = band
+// kernel never stacked, 4 = band kernel stacked but never streaming, 5 =
+// streaming wherever it applies, however short its segments
+// (glbm_nn_tc_set_variant).
+__attribute__((visibility("hidden"))) int g_tc_variant = 0;
 
 namespace {
 
@@ -1185,11 +1191,6 @@ bool map_act_band(CUtensorMap *m, const void *ptr, int c, int w, int h, int n, i
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// 0 = choose per layer, 1 = tile kernel only, 2 = as 0 with the tile
-// kernel's ring never deepened, 3 = band kernel never stacked, 4 = band
-// kernel stacked but never streaming, 5 = streaming wherever it applies,
-// however short its segments (glbm_nn_tc_set_variant).
-int g_tc_variant = 0;
 // dynamic shared memory budget: the 227 KB opt-in limit less room for the
 // kernels' static shared memory
 constexpr size_t kSmemLimit = 226 * 1024;

@@ -19,8 +19,10 @@
 
 extern __attribute__((visibility("hidden"))) thread_local char g_create_err[512];
 
-// defined in nn_tc.cu, library-internal
+// defined in nn_tc.cu, library-internal: the debug-starve test hook and the
+// kernel choice of glbm_nn_tc_set_variant
 extern int g_tc_starve;
+extern int g_tc_variant;
 
 namespace {
 

@@ -54,11 +54,18 @@ WG_CASES = [
     (1, 8, 64, 128, 128, 3),   # wide layer, 4 output boxes
     (2, 12, 40, 32, 3, 1),     # 1x1 head, 3 real output channels padded to 32
     (1, 4, 16, 256, 256, 3),   # the widest channel counts, image narrower than a step
+    (2, 10, 24, 96, 32, 3),    # 3 input chunks in groups of 2 (a partial group), one ragged step
+    (1, 5, 8, 64, 96, 3),      # 3 output chunks in groups of 2, 16-pixel steps wider than the image
+    (3, 1, 50, 32, 64, 3),     # one-row images: every x row above and below is padding
 ]
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["band", "taps"])
 @pytest.mark.parametrize("n,h,w,cin,cout,k", WG_CASES)
-def test_wgrad_matches_oracle(pkg, n, h, w, cin, cout, k):
+def test_wgrad_matches_oracle(pkg, n, h, w, cin, cout, k, variant):
+    """variant 0: 3x3 gradients in the band form (every tap in one MMA);
+    variant 1: one (tap, chunk) box per M atom.  1x1 layers take the second
+    form either way."""
     import torch
     lib = pkg.load()
     rng = np.random.default_rng(hash((n, h, w, cin, cout, k)) % 2 ** 32)
@@ -70,7 +77,11 @@ def test_wgrad_matches_oracle(pkg, n, h, w, cin, cout, k):
     xd, dyd = _nhwc(x, cx), _nhwc(dy, cy)
     dw = torch.full((cout * cin * k * k,), 0.25, dtype=torch.float32, device="cuda")  # accumulates
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rc = lib.glbm_nn_tc_conv_wgrad(_vp(xd), cx, cin, _vp(dyd), cy, cout, n, h, w, k, _vp(dw), _vp(err), _st())
+    lib.glbm_nn_tc_set_variant(variant)
+    try:
+        rc = lib.glbm_nn_tc_conv_wgrad(_vp(xd), cx, cin, _vp(dyd), cy, cout, n, h, w, k, _vp(dw), _vp(err), _st())
+    finally:
+        lib.glbm_nn_tc_set_variant(0)
     assert rc == 0, lib.glbm_last_error(None)
     dyf = torch.from_numpy(dy.astype(np.float32)).cuda()
     dbd = torch.zeros(cout, dtype=torch.float32, device="cuda")

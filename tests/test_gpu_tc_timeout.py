@@ -77,11 +77,14 @@ def test_conv_timeout_reports_and_context_survives(pkg, kind, variant, n, h, w, 
     assert torch.equal(y0, y2)
 
 
-def test_wgrad_timeout_reports_and_context_survives(pkg):
+@pytest.mark.parametrize("variant", [0, 1], ids=["band", "taps"])
+def test_wgrad_timeout_reports_and_context_survives(pkg, variant):
     import torch
     lib = pkg.load()
+    lib.glbm_nn_tc_set_variant(variant)
     rng = np.random.default_rng(3)
-    n, h, w, cin, cout = 2, 16, 32, 32, 32
+    # large enough that the first CTA of either form loads at least two stages
+    n, h, w, cin, cout = 8, 256, 64, 32, 32
     x = torch.from_numpy(rng.normal(size=(n, h, w, cin)).astype(np.float32)).to(torch.bfloat16).cuda()
     dy = torch.from_numpy(rng.normal(size=(n, h, w, cout)).astype(np.float32)).to(torch.bfloat16).cuda()
 
@@ -103,6 +106,8 @@ def test_wgrad_timeout_reports_and_context_survives(pkg):
         dw2, e2 = run()
     finally:
         lib.glbm_nn_tc_debug_starve(0)
+        lib.glbm_nn_tc_set_variant(0)
     assert e2 == 0
-    # FP32 atomics from several CTAs: the same sums in another order at most
-    assert torch.allclose(dw0, dw2, rtol=1e-5, atol=1e-5)
+    # FP32 atomics from several hundred CTAs: the same sums in another order,
+    # each partial rounded at 2^-24 of the largest magnitude at most
+    assert torch.allclose(dw0, dw2, rtol=0, atol=1e-4 * float(dw0.abs().max()))
