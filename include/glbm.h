@@ -555,7 +555,8 @@ void glbm_nn_tc_debug_starve(int stage);
  * 32-channel chunk; stacked taps for 32 output channels); the rest run the
  * tile kernel (one 128-pixel tile per CTA, one TMA tile per tap; a 3-stage
  * TMA ring, or an 8-stage one when the grid has at most one CTA per SM);
- * 1 = tile kernel always; 2 = as 0 but the tile kernel always with the
+ * 1 = tile kernel always (and glbm_nn_tc_conv_wgrad in its per-tap form);
+ * 2 = as 0 but the tile kernel always with the
  * 3-stage ring; 3 = band kernel where it applies but never stacked or
  * streaming; 4 = band kernel, stacked, never streaming; 5 = as 0 with
  * streaming however short its segments.  All compute the same convolution;
@@ -574,9 +575,14 @@ glbm_status glbm_nn_tc_pack_weights(const float *w, int cout, int cin,
  * channels (pixel stride cx, a multiple of 32; the first cin are real), dy
  * with cy channels (a multiple of 32, <= 256; the first cout are real).  dw
  * is FP32 [cout][cin][k][k] on the device and is accumulated into (FP32
- * atomics: the last bits depend on the order).  FP32 accumulation of BF16
- * products in tensor memory.  *err as in glbm_nn_tc_conv.  16-byte aligned
- * x and dy.  EINVAL for bad sizes. */
+ * reductions from many CTAs: the last bits depend on their order; 16-byte
+ * vector reductions where cin is a multiple of 4 and dw is 16-byte
+ * aligned).  FP32 accumulation of BF16 products in tensor memory.  3x3
+ * layers run in band form: each CTA loads bands of 8 (or 4, 2, 1) dy rows
+ * and the input rows they meet once, and one MMA covers all nine taps of a
+ * 32-channel input chunk and output chunk; with glbm_nn_tc_set_variant(1),
+ * and for 1x1 layers, one MMA atom per (tap, 32-channel chunk).  *err as in
+ * glbm_nn_tc_conv.  16-byte aligned x and dy.  EINVAL for bad sizes. */
 glbm_status glbm_nn_tc_conv_wgrad(const void *x, int cx, int cin,
                                   const void *dy, int cy, int cout, int n,
                                   int h, int w, int k, float *dw, int *err,

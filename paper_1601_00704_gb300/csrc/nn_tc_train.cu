@@ -23,6 +23,12 @@
 // and the last bits of dW, vary from run to run).  Roles: warp 0 issues TMA,
 // warp 1 issues the MMAs and commits, warps 2-5 read the accumulator; every
 // wait is bounded as in nn_tc.cu.
+//
+// That per-tap form (k_tc_wgrad) serves 1x1 layers and variant 1.  3x3
+// layers run in the band form (k_tc_wgrad_band, below), which puts the taps
+// into the MMA's M and N instead: three consecutive input rows along M, three
+// one-pixel shifts of a dy row along N, all nine taps in one MMA, each input
+// and dy row loaded once per band.
 
 #include "tc_common.cuh"
 

@@ -167,6 +167,77 @@ def time_training(batches, batch, n, base, levels, max_ch, seed=0):
     return out
 
 
+def time_layers(n, batch, base, levels, max_ch, reps=20, only=None):
+    """CUDA-event times of the network's 3x3 layers after the first (level l
+    at (n >> l)^2, `batch` random images, BF16 NHWC operands), through the
+    library's entry points: the forward convolution with bias and ReLU under
+    each kernel choice of glbm_nn_tc_set_variant (1 = tile, 3 = band, 0 =
+    default), and the weight gradient in its two forms (1 = per tap, 0 =
+    band).  3 warm-up calls, then `reps` timed calls of each; `only` keeps
+    the named layers."""
+    import ctypes as C
+    import torch
+    from paper_1601_00704_gb300 import load, surrogate
+    lib = load()
+    net = surrogate.UNet(base=base, levels=levels, max_ch=max_ch)
+    vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def timed(call):
+        for _ in range(3):
+            if call() != 0:
+                raise RuntimeError(lib.glbm_last_error(None).decode())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            call()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    out = {"n": n, "batch": batch, "reps": reps, "layers": {}}
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    try:
+        for name, ci, co, k in net.specs:
+            if k != 3 or name == "e0a" or (only and name not in only):
+                continue
+            lvl = int(name[1:-1])
+            s = n >> lvl
+            c0, c1 = (net.ch[lvl + 1], net.ch[lvl]) if name.startswith("d") and name.endswith("a") else (ci, 0)
+            x0 = torch.randn(batch, s, s, c0, device="cuda").to(torch.bfloat16)
+            x1 = torch.randn(batch, s, s, c1, device="cuda").to(torch.bfloat16) if c1 else None
+            wf = torch.randn(co * ci * 9, device="cuda") * (2.0 / (ci * 9)) ** 0.5
+            wt = torch.empty(9 * co * ci, dtype=torch.bfloat16, device="cuda")
+            if lib.glbm_nn_tc_pack_weights(vp(wf), co, ci, 3, co, ci, vp(wt), st) != 0:
+                raise RuntimeError(lib.glbm_last_error(None).decode())
+            b = torch.zeros(co, device="cuda")
+            y = torch.empty(batch, s, s, co, dtype=torch.bfloat16, device="cuda")
+            gflop = 2.0 * batch * s * s * ci * co * 9 / 1e9
+            rec = {"size": s, "cin": ci, "cout": co, "gflop": gflop, "conv_us": {}, "wgrad_us": {}}
+            for v, key in ((1, "tile"), (3, "band"), (0, "default")):
+                lib.glbm_nn_tc_set_variant(v)
+                rec["conv_us"][key] = timed(lambda: lib.glbm_nn_tc_conv(
+                    vp(x0), c0, vp(x1), c1, batch, s, s, 3, vp(wt), vp(b), co, vp(y), co, 1, 0, 0, vp(err), st))
+            x = torch.cat((x0, x1), dim=3).contiguous() if c1 else x0
+            dy = torch.randn(batch, s, s, co, device="cuda").to(torch.bfloat16)
+            dw = torch.zeros(co * ci * 9, device="cuda")
+            for v, key in ((1, "taps"), (0, "band")):
+                lib.glbm_nn_tc_set_variant(v)
+                rec["wgrad_us"][key] = timed(lambda: lib.glbm_nn_tc_conv_wgrad(
+                    vp(x), ci, ci, vp(dy), co, co, batch, s, s, 3, vp(dw), vp(err), st))
+            lib.glbm_nn_tc_set_variant(0)
+            torch.cuda.synchronize()
+            if int(err.item()) != 0:
+                raise RuntimeError(f"{name}: a tensor-core pipeline wait timed out (code {int(err.item())})")
+            for part in ("conv", "wgrad"):
+                rec[part + "_tflops"] = {key: gflop / us * 1e3 for key, us in rec[part + "_us"].items()}
+            out["layers"][name] = rec
+    finally:
+        lib.glbm_nn_tc_set_variant(0)
+    return out
+
+
 def predict(net, eps, K, tc=False):
     """Warm-start fields (rho, ux, uy) as host arrays for one medium of any
     size (multiple of 2^(levels-1)); tc runs the network on the tensor cores."""
@@ -208,6 +279,11 @@ def main(argv=None):
     p.add_argument("--time-epoch", type=int, metavar="BATCHES",
                    help="time BATCHES training steps (batch --batch, --n^2 random data) with the FP32 kernels "
                         "and with the tensor cores, then exit")
+    p.add_argument("--time-layers", type=int, metavar="N",
+                   help="time the tensor-core convolution kernels and weight-gradient forms of every 3x3 layer "
+                        "after the first at N x N (level l at N >> l), batch --batch, then exit")
+    p.add_argument("--reps", type=int, default=20, help="timed calls per kernel for --time-layers")
+    p.add_argument("--layers", help="comma-separated layer names for --time-layers (default: all)")
     a = p.parse_args(argv)
     from paper_1601_00704_gb300 import build
     build.build()
@@ -219,6 +295,10 @@ def main(argv=None):
         return
     if a.time_epoch:
         print(json.dumps(time_training(a.time_epoch, a.batch, a.n, a.base, a.levels, a.max_ch)))
+        return
+    if a.time_layers:
+        only = set(a.layers.split(",")) if a.layers else None
+        print(json.dumps(time_layers(a.time_layers, a.batch, a.base, a.levels, a.max_ch, a.reps, only)))
         return
     if a.study_only:
         net = surrogate.UNet(base=a.base, levels=a.levels, max_ch=a.max_ch)

@@ -161,3 +161,18 @@ def test_unet_tc_gradients_match_oracle(pkg, levels, max_ch, size, batch):
     assert worst < 1e-1
     assert total < 3e-2
     assert cos > 0.999
+
+
+def test_time_layers_runs_every_kernel_choice(pkg):
+    """The per-layer timing mode of train_surrogate runs each convolution
+    kernel choice and both weight-gradient forms on the chosen layers and
+    reports positive times."""
+    from paper_1601_00704_gb300 import train_surrogate as T
+    out = T.time_layers(64, 2, 32, 6, 128, reps=1, only={"e1b", "d0a"})
+    assert set(out["layers"]) == {"e1b", "d0a"}
+    d0a = out["layers"]["d0a"]
+    assert (d0a["size"], d0a["cin"], d0a["cout"]) == (64, 96, 32)
+    for rec in out["layers"].values():
+        assert set(rec["conv_us"]) == {"tile", "band", "default"}
+        assert set(rec["wgrad_us"]) == {"taps", "band"}
+        assert all(v > 0 for v in list(rec["conv_us"].values()) + list(rec["wgrad_us"].values()))
