@@ -95,6 +95,36 @@ def test_wgrad_matches_oracle(pkg, n, h, w, cin, cout, k, variant):
     np.testing.assert_allclose(dbd.cpu().numpy(), db, rtol=1e-5, atol=1e-4)
 
 
+def test_wgrad_band_unaligned_dw_matches_oracle(pkg):
+    """dw one float past a 16-byte boundary: the band form's epilogue falls
+    back from 16-byte vector reductions to scalar ones (cin % 4 == 0 would
+    otherwise take the vector path) and still accumulates the oracle's
+    gradient."""
+    import torch
+    lib = pkg.load()
+    n, h, w, cin, cout = 2, 11, 40, 64, 32
+    rng = np.random.default_rng(11)
+    x = _bf16(rng.normal(size=(n, cin, h, w)))
+    dy = _bf16(rng.normal(size=(n, cout, h, w)))
+    W = np.zeros((cout, cin, 3, 3))
+    _, dW, _ = ou.conv_backward(x, W, dy)
+    xd, dyd = _nhwc(x, cin), _nhwc(dy, cout)
+    buf = torch.full((cout * cin * 9 + 4,), -1.0, dtype=torch.float32, device="cuda")
+    buf[1:1 + cout * cin * 9] = 0.0
+    dw = buf[1:]
+    assert dw.data_ptr() % 16 == 4
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.glbm_nn_tc_conv_wgrad(_vp(xd), cin, cin, _vp(dyd), cout, cout, n, h, w, 3, _vp(dw), _vp(err), _st())
+    assert rc == 0, lib.glbm_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    out = buf.cpu().numpy().astype(np.float64)
+    assert out[0] == -1.0 and np.all(out[1 + cout * cin * 9:] == -1.0)  # nothing outside dw written
+    got = out[1:1 + cout * cin * 9].reshape(cout, cin, 3, 3)
+    mag = ou.conv_backward(np.abs(x), W, np.abs(dy))[1]
+    np.testing.assert_allclose(got, dW, rtol=0, atol=1e-5 * mag.max() + 1e-6)
+
+
 def test_pack_weights_flip(pkg):
     import torch
     lib = pkg.load()
