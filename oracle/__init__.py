@@ -23,8 +23,10 @@ Parity status per function (pins in ``tests/test_oracle_*.py``):
                          layers (exact momentum balance), Taylor-Green decay
                          (viscosity), mass conservation, D2Q9 BGK+Guo
                          textbook reduction (eps = 1, K = inf).
-* two-phase random media (the benchmark workload) - parity unpinned beyond
-  the invariants above: there the oracle itself is the reference.
+* two-phase random media (the benchmark workload) - no closed form for the
+  fields; pinned by the exact domain momentum balance (sum of rho F = 0 at
+  steady state, F from Eq. 27, with and without Forchheimer drag) besides
+  the invariants above.
 """
 
 from __future__ import annotations

@@ -47,8 +47,9 @@
  * Eq. 33 root, Darcy and Forchheimer fixed points, exact Poiseuille at
  * tau = 1/2 + sqrt(3)/4, Brinkman channel convergence, series-layer momentum
  * balance, Taylor-Green viscosity, mass conservation, and the reduction to
- * textbook D2Q9 BGK with Guo forcing.  On two-phase random media the result
- * has no closed form: parity unpinned beyond those invariants.
+ * textbook D2Q9 BGK with Guo forcing.  On two-phase random media the fields
+ * have no closed form; there the steady state is pinned by the exact domain
+ * momentum balance (sum of rho F = 0, F from Eq. 27).
  *
  * Build: gcc -O2 -shared -fPIC (single thread, parity) or with -fopenmp
  * (rows in parallel, timing only); results are bitwise identical because

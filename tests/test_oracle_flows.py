@@ -143,6 +143,31 @@ def test_series_layers_momentum_balance(orc):
     assert o.permeability() == pytest.approx(keff, rel=1e-4)
 
 
+@pytest.mark.parametrize("G,F_eps", [(1e-5, 0.0), (1e-4, 2.0)], ids=["darcy", "forchheimer"])
+def test_two_phase_medium_momentum_balance(orc, G, F_eps):
+    """The benchmark's two-phase OM/IOM medium (32 x 32, periodic x and y),
+    for which the steady state has no closed form: the same exact balance
+    as the series layers, sum over nodes of rho F = 0 in both directions,
+    with F from Eq. 27 evaluated here on the oracle's converged u.  The
+    Forchheimer case checks that the balance resolves its drag: the
+    quadratic term's share of the sum is orders of magnitude above the
+    residual."""
+    eps, K, _ = media.two_phase_medium(32, 32, seed=3)
+    tau = 1.0
+    nu = (tau - 0.5) / 3
+    o = run(orc, eps, K, (G, 0.0), tau=tau, periodic_y=True, steps=300000, tol=1e-14, feps=F_eps)
+    speed = np.hypot(o.ux, o.uy)
+    drag = eps * nu / K + eps * F_eps / np.sqrt(K) * speed
+    Fx = eps * G - drag * o.ux
+    Fy = -drag * o.uy
+    drive = np.sum(o.rho * eps * G)
+    bound = 1e-11 * drive
+    assert abs(np.sum(o.rho * Fx)) < bound
+    assert abs(np.sum(o.rho * Fy)) < bound
+    if F_eps:
+        assert np.sum(o.rho * eps * F_eps / np.sqrt(K) * speed * o.ux) > 1e3 * bound
+
+
 def test_parallel_layers_arithmetic_mean(orc):
     """Layers parallel to the flow, periodic y (the 'parallel' arrangement):
     away from Brinkman layers of width sqrt(K/eps) each layer carries its
