@@ -25,6 +25,10 @@
  *    state is unchanged unless stated.
  *  - A handle is not thread-safe; use one handle per host thread / stream.
  *    Work is enqueued on the stream given to glbm_create.
+ *  - The solver and batch entry points (set_medium, init_equilibrium, step,
+ *    mean_velocity, permeability, save, load, batch_set_medium, batch_step)
+ *    each open an NVTX range of their own name for a profiler's timeline;
+ *    without a tool attached the ranges record nothing.
  */
 #ifndef GLBM_H
 #define GLBM_H

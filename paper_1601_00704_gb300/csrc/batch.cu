@@ -15,6 +15,7 @@
 // Forchheimer-free model of Eq. 28 only.
 
 #include "glbm.h"
+#include "trace.h"
 #include "glbm_kernels.cuh"
 #include "setup_kernels.cuh"
 
@@ -683,6 +684,7 @@ glbm_status glbm_batch_create(int count, const int *nx, const int *ny, double ta
 }
 
 glbm_status glbm_batch_set_medium(glbm_batch_t h, int index, const double *eps, const double *K, int device_ptrs) {
+    glbm_trace::Range trace_range("glbm_batch_set_medium");
     if (glbm_status s = bcheck(h)) return s;
     if (index < 0 || index >= h->count) return bfail(h, GLBM_EINVAL, "batch_set_medium: index %d out of range", index);
     if (!eps || !K) return bfail(h, GLBM_EINVAL, "batch_set_medium: eps and K are required");
@@ -767,6 +769,7 @@ glbm_status glbm_batch_get_persistent(glbm_batch_t h, int *on) {
 
 glbm_status glbm_batch_step(glbm_batch_t h, long long n, double tol, int check_every, long long *steps_done,
                             int *active_left) {
+    glbm_trace::Range trace_range("glbm_batch_step");
     if (steps_done) *steps_done = 0;
     if (glbm_status s = bcheck(h)) return s;
     for (int m = 0; m < h->count; ++m)

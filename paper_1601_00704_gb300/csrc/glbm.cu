@@ -4,6 +4,7 @@
 // are in glbm_kernels.cuh; the C ABI is declared in include/glbm.h.
 
 #include "glbm.h"
+#include "trace.h"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -512,6 +513,7 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
 }
 
 glbm_status glbm_set_medium(glbm_t h, const double *eps, const double *K, double F_eps, int device_ptrs) {
+    glbm_trace::Range trace_range("glbm_set_medium");
     if (glbm_status s = check(h)) return s;
     if (!eps || !K) return fail(h, GLBM_EINVAL, "set_medium: eps and K are required");
     if (!std::isfinite(F_eps)) return fail(h, GLBM_EINVAL, "set_medium: F_eps must be finite");
@@ -569,6 +571,7 @@ glbm_status glbm_set_force(glbm_t h, double gx, double gy) {
 
 glbm_status glbm_init_equilibrium(glbm_t h, const double *rho, const double *ux, const double *uy,
                                   int device_ptrs) {
+    glbm_trace::Range trace_range("glbm_init_equilibrium");
     if (glbm_status s = check(h)) return s;
     if (!h->has_medium) return fail(h, GLBM_ESTATE, "init_equilibrium: no medium set");
     if ((ux == nullptr) != (uy == nullptr))
@@ -612,6 +615,7 @@ glbm_status glbm_init_equilibrium(glbm_t h, const double *rho, const double *ux,
 
 glbm_status glbm_step(glbm_t h, long long n, double tol, int check_every, long long *steps_done,
                       int *converged) {
+    glbm_trace::Range trace_range("glbm_step");
     if (steps_done) *steps_done = 0;
     if (converged) *converged = 0;
     if (glbm_status s = check(h)) return s;
@@ -660,6 +664,7 @@ glbm_status glbm_set_convergence(glbm_t h, int patience) {
 }
 
 glbm_status glbm_mean_velocity(glbm_t h, double out[2]) {
+    glbm_trace::Range trace_range("glbm_mean_velocity");
     if (glbm_status s = check(h)) return s;
     if (!out) return fail(h, GLBM_EINVAL, "mean_velocity: out is NULL");
     if (!h->reduced) return fail(h, GLBM_ESTATE, "mean_velocity: no step has completed since the last reset");
@@ -671,6 +676,7 @@ glbm_status glbm_mean_velocity(glbm_t h, double out[2]) {
 }
 
 glbm_status glbm_permeability(glbm_t h, double *kxx) {
+    glbm_trace::Range trace_range("glbm_permeability");
     if (glbm_status s = check(h)) return s;
     if (!kxx) return fail(h, GLBM_EINVAL, "permeability: kxx is NULL");
     if (h->gx == 0.0) return fail(h, GLBM_EINVAL, "permeability: G_x is zero");
@@ -789,6 +795,7 @@ struct File {
 extern "C" {
 
 glbm_status glbm_save(glbm_t h, const char *path) {
+    glbm_trace::Range trace_range("glbm_save");
     if (glbm_status s = check(h)) return s;
     if (!path) return fail(h, GLBM_EINVAL, "save: path is NULL");
     if (!h->has_medium) return fail(h, GLBM_ESTATE, "save: no medium set");
@@ -835,6 +842,7 @@ glbm_status glbm_save(glbm_t h, const char *path) {
 }
 
 glbm_status glbm_load(glbm_t h, const char *path) {
+    glbm_trace::Range trace_range("glbm_load");
     if (glbm_status s = check(h)) return s;
     if (!path) return fail(h, GLBM_EINVAL, "load: path is NULL");
     File f;
