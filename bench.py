@@ -82,6 +82,8 @@ def args_():
                    help="skip the batched-media (DGM/GMS sweep) measurement")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-steps", type=int, default=500)
+    p.add_argument("--jsonl", metavar="PATH",
+                   help="also append the result line to this JSON-lines file (one record per run)")
     p.add_argument("--sweep", type=int, default=0, metavar="STEPS",
                    help="also run the 25-cell medium sweep (OM fraction x correlation length at nx x ny), "
                         "each cell up to STEPS time steps or converged (off by default: minutes)")
@@ -582,8 +584,17 @@ def run_reference(a, world, rank):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
-    print(json.dumps(line), flush=True)
+    emit(line, a)
     return 0
+
+
+def emit(line, a):
+    """The one JSON result line on stdout and, with --jsonl, appended to that file."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if a.jsonl:
+        with open(a.jsonl, "a") as fh:
+            fh.write(text + "\n")
 
 
 def run_ours(a, world, rank, local):
@@ -700,7 +711,7 @@ def run_ours(a, world, rank, local):
         }
         if swp is not None:
             line["sweep"] = swp
-        print(json.dumps(line), flush=True)
+        emit(line, a)
     return 0
 
 
