@@ -253,6 +253,18 @@ void glbm_destroy(glbm_t h);
  */
 void glbm_debug_fail_launch(long long after);
 
+/*
+ * Memory-safety check without a sanitizer (no counterpart in the paper):
+ * every device buffer a handle allocates (distributions, coefficients,
+ * reduction scratch, status words, input staging) carries 4 KB guard zones
+ * before and after it, filled with the byte 0xA5 when allocated.  Sets
+ * *damaged to the number of guard bytes that no longer hold it: 0 unless a
+ * kernel or copy wrote outside its buffer.  poke != 0 first overwrites one
+ * guard byte (and restores it after counting), so that *damaged = 1 shows
+ * the count works.  Waits for the handle's stream.
+ */
+glbm_status glbm_debug_guards(glbm_t h, int poke, long long *damaged);
+
 /* ===========================================================================
  * Batched media: many lattices of uneven size advanced together.
  *
@@ -305,6 +317,9 @@ glbm_status glbm_batch_set_schedule(glbm_batch_t b, int threads, int order);
  * glbm_batch_get_persistent reports the current choice. */
 glbm_status glbm_batch_set_persistent(glbm_batch_t b, int on);
 glbm_status glbm_batch_get_persistent(glbm_batch_t b, int *on);
+
+/* glbm_debug_guards for the batch's device buffers. */
+glbm_status glbm_batch_debug_guards(glbm_batch_t b, int poke, long long *damaged);
 
 /* Time every schedule (threads x order x persistent or not) for
  * 2 x trial_steps steps on this batch, keep the fastest (threads/order

@@ -34,7 +34,8 @@ SYMBOLS = ["glbm_create", "glbm_set_medium", "glbm_set_force",
            "glbm_init_equilibrium", "glbm_step", "glbm_mean_velocity",
            "glbm_permeability", "glbm_get_velocity", "glbm_get_distributions",
            "glbm_counters", "glbm_destroy", "glbm_last_error",
-           "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_save", "glbm_load",
+           "glbm_step_reduce_noalloc", "glbm_debug_fail_launch", "glbm_debug_guards",
+           "glbm_batch_debug_guards", "glbm_save", "glbm_load",
            "glbm_set_convergence", "glbm_batch_set_persistent", "glbm_batch_get_persistent",
            "glbm_batch_set_convergence", "glbm_nn_tc_set_variant",
            "glbm_nn_tc_conv_wgrad", "glbm_nn_tc_pack_weights_flip", "glbm_nn_bias_grad",
@@ -90,6 +91,8 @@ def load(path: str | None = None) -> C.CDLL:
         "glbm_counters": ([h, C.POINTER(ll), C.POINTER(ll)], i),
         "glbm_destroy": ([h], None),
         "glbm_debug_fail_launch": ([ll], None),
+        "glbm_debug_guards": ([h, i, C.POINTER(ll)], i),
+        "glbm_batch_debug_guards": ([h, i, C.POINTER(ll)], i),
         "glbm_save": ([h, C.c_char_p], i),
         "glbm_set_convergence": ([h, i], i),
         "glbm_batch_set_persistent": ([h, i], i),
@@ -318,6 +321,14 @@ class Solver:
         self._check(self._lib.glbm_counters(self._h, C.byref(s), C.byref(l)))
         return s.value, l.value
 
+    def guard_damage(self, poke=False):
+        """Guard-zone bytes around the handle's device buffers that no longer
+        hold their fill pattern (0 unless something wrote out of bounds);
+        poke=True damages one byte first to show the count works."""
+        d = C.c_longlong()
+        self._check(self._lib.glbm_debug_guards(self._h, int(bool(poke)), C.byref(d)))
+        return d.value
+
 
 class Batch:
     """Many media of uneven size advanced together (a ``glbm_batch_t``).
@@ -398,6 +409,12 @@ class Batch:
         self._check(self._lib.glbm_batch_step(self._h, int(n), float(tol), int(check_every),
                                               C.byref(done), C.byref(left)))
         return done.value, left.value
+
+    def guard_damage(self, poke=False):
+        """As Solver.guard_damage, for the batch's device buffers."""
+        d = C.c_longlong()
+        self._check(self._lib.glbm_batch_debug_guards(self._h, int(bool(poke)), C.byref(d)))
+        return d.value
 
     def results(self):
         """-> dict of per-medium arrays: kxx, mean_u (count x 2), steps, converged."""

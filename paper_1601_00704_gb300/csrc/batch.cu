@@ -15,6 +15,7 @@
 // Forchheimer-free model of Eq. 28 only.
 
 #include "glbm.h"
+#include "guard.h"
 #include "trace.h"
 #include "glbm_kernels.cuh"
 #include "setup_kernels.cuh"
@@ -285,6 +286,7 @@ struct glbm_batch {
     StepClock *dclock = nullptr;
     int *dflag = nullptr;
     double *stage = nullptr;
+    glbm_guard::Table guards;  // every device buffer of the batch, with its guard zones
     long long stage_n = 0;
     int parity = 0;
     long long tstep = 0;
@@ -560,10 +562,10 @@ glbm_status bcheck(glbm_batch *h) {
 
 void brelease(glbm_batch *h) {
     drop_graphs(h);
-    for (auto &p : h->buf) if (p) cudaFree(p), p = nullptr;
-    for (auto &p : h->coef) if (p) cudaFree(p), p = nullptr;
+    for (auto &p : h->buf) glbm_guard::release(h->guards, p), p = nullptr;
+    for (auto &p : h->coef) glbm_guard::release(h->guards, p), p = nullptr;
     void *ptrs[] = {h->dmed, h->dtiles, h->dact, h->partial, h->dstat, h->dclock, h->dflag, h->stage, h->dbar, h->derr};
-    for (void *p : ptrs) if (p) cudaFree(p);
+    for (void *p : ptrs) glbm_guard::release(h->guards, p);
     h->dmed = nullptr;
     h->dtiles = nullptr;
     h->dact = nullptr;
@@ -651,19 +653,22 @@ glbm_status glbm_batch_create(int count, const int *nx, const int *ny, double ta
     } else {
         h->stream = static_cast<cudaStream_t>(stream);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], offf * h->elem);
-    if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], offf * h->elem);
-    if (e == cudaSuccess) e = cudaMalloc(&h->coef[0], offc * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->coef[1], offc * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dmed, sizeof(BMed) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&h->dtiles, sizeof(BTile) * maxt);
-    if (e == cudaSuccess) e = cudaMalloc(&h->dact, sizeof(int) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&h->partial, sizeof(double) * 2 * maxt);
-    if (e == cudaSuccess) e = cudaMalloc(&h->dstat, sizeof(DevStatus) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&h->dclock, sizeof(StepClock));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dbar, sizeof(GridBar));
-    if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
+    auto galloc = [h](auto **p, size_t bytes) {
+        return glbm_guard::alloc(h->guards, reinterpret_cast<void **>(p), bytes, h->stream);
+    };
+    if (e == cudaSuccess) e = galloc(&h->buf[0], offf * h->elem);
+    if (e == cudaSuccess) e = galloc(&h->buf[1], offf * h->elem);
+    if (e == cudaSuccess) e = galloc(&h->coef[0], offc * sizeof(float));
+    if (e == cudaSuccess) e = galloc(&h->coef[1], offc * sizeof(float));
+    if (e == cudaSuccess) e = galloc(&h->dmed, sizeof(BMed) * count);
+    if (e == cudaSuccess) e = galloc(&h->dtiles, sizeof(BTile) * maxt);
+    if (e == cudaSuccess) e = galloc(&h->dact, sizeof(int) * count);
+    if (e == cudaSuccess) e = galloc(&h->partial, sizeof(double) * 2 * maxt);
+    if (e == cudaSuccess) e = galloc(&h->dstat, sizeof(DevStatus) * count);
+    if (e == cudaSuccess) e = galloc(&h->dclock, sizeof(StepClock));
+    if (e == cudaSuccess) e = galloc(&h->dflag, sizeof(int));
+    if (e == cudaSuccess) e = galloc(&h->dbar, sizeof(GridBar));
+    if (e == cudaSuccess) e = galloc(&h->derr, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dbar, 0, sizeof(GridBar), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev);
@@ -692,7 +697,9 @@ glbm_status glbm_batch_set_medium(glbm_batch_t h, int index, const double *eps, 
     const long long N = (long long)md.nx * md.ny;
     const double *de = eps, *dk = K;
     if (!device_ptrs) {
-        if (!h->stage) BCU(h, cudaMalloc(&h->stage, sizeof(double) * 2 * h->stage_n));
+        if (!h->stage)
+            BCU(h, glbm_guard::alloc(h->guards, reinterpret_cast<void **>(&h->stage), sizeof(double) * 2 * h->stage_n,
+                                     h->stream));
         BCU(h, cudaMemcpyAsync(h->stage, eps, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
         BCU(h, cudaMemcpyAsync(h->stage + h->stage_n, K, sizeof(double) * N, cudaMemcpyHostToDevice, h->stream));
         de = h->stage;
@@ -764,6 +771,13 @@ glbm_status glbm_batch_set_convergence(glbm_batch_t h, int patience) {
 glbm_status glbm_batch_get_persistent(glbm_batch_t h, int *on) {
     if (!h || !on) return GLBM_EINVAL;
     *on = h->persistent ? 1 : 0;
+    return GLBM_OK;
+}
+
+glbm_status glbm_batch_debug_guards(glbm_batch_t h, int poke, long long *damaged) {
+    if (glbm_status s = bcheck(h)) return s;
+    if (!damaged) return bfail(h, GLBM_EINVAL, "batch_debug_guards: damaged is required");
+    BCU(h, glbm_guard::count_damage(h->guards, h->stream, poke, damaged));
     return GLBM_OK;
 }
 

@@ -4,6 +4,7 @@
 // are in glbm_kernels.cuh; the C ABI is declared in include/glbm.h.
 
 #include "glbm.h"
+#include "guard.h"
 #include "trace.h"
 
 #include <cuda_bf16.h>
@@ -64,6 +65,7 @@ struct glbm {
     DevStatus *hstat = nullptr;  // pinned
     int *dflag = nullptr;
     double *stage = nullptr;  // 3*N doubles of input staging, allocated on first host input
+    glbm_guard::Table guards; // every device buffer above, with its guard zones
     bool has_medium = false, forch = false, reduced = false;
     double feps_mode = 0.0, gx = 0.0, gy = 0.0;
     double scale = 1.0;       // FP16 storage scale S (stored = g*S)
@@ -392,7 +394,9 @@ void launch_export(glbm *h, double *f) {
 glbm_status stage_inputs(glbm *h, const double *const *src, const double **dst, int k, int device_ptrs) {
     bool any = false;
     for (int j = 0; j < k; ++j) any = any || src[j];
-    if (any && !device_ptrs && !h->stage) CU(h, cudaMalloc(&h->stage, sizeof(double) * 3 * size_t(h->N)));
+    if (any && !device_ptrs && !h->stage)
+        CU(h, glbm_guard::alloc(h->guards, reinterpret_cast<void **>(&h->stage), sizeof(double) * 3 * size_t(h->N),
+                                h->stream));
     for (int j = 0; j < k; ++j) {
         if (!src[j] || device_ptrs) {
             dst[j] = src[j];
@@ -439,14 +443,15 @@ glbm_status launch_error(glbm *h) {
 
 void release(glbm *h) {
     drop_graphs(h);
-    for (auto &p : h->buf) if (p) cudaFree(p), p = nullptr;
-    for (auto &p : h->coef) if (p) cudaFree(p), p = nullptr;
-    if (h->partial) cudaFree(h->partial), h->partial = nullptr;
-    if (h->pmax) cudaFree(h->pmax), h->pmax = nullptr;
-    if (h->dstat) cudaFree(h->dstat), h->dstat = nullptr;
-    if (h->dflag) cudaFree(h->dflag), h->dflag = nullptr;
-    if (h->dclock) cudaFree(h->dclock), h->dclock = nullptr;
-    if (h->stage) cudaFree(h->stage), h->stage = nullptr;
+    glbm_guard::Table &g = h->guards;
+    for (auto &p : h->buf) glbm_guard::release(g, p), p = nullptr;
+    for (auto &p : h->coef) glbm_guard::release(g, p), p = nullptr;
+    glbm_guard::release(g, h->partial), h->partial = nullptr;
+    glbm_guard::release(g, h->pmax), h->pmax = nullptr;
+    glbm_guard::release(g, h->dstat), h->dstat = nullptr;
+    glbm_guard::release(g, h->dflag), h->dflag = nullptr;
+    glbm_guard::release(g, h->dclock), h->dclock = nullptr;
+    glbm_guard::release(g, h->stage), h->stage = nullptr;
     if (h->hstat) cudaFreeHost(h->hstat), h->hstat = nullptr;
 }
 
@@ -488,14 +493,17 @@ glbm_status glbm_create(int nx, int ny, double tau, glbm_storage storage, unsign
     // the scalar grid has the most blocks
     const Geo g1 = make_geo(h, 1);
     h->nparts_max = g1.bpr * g1.ny;
-    if (e == cudaSuccess) e = cudaMalloc(&h->buf[0], fbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], fbytes);
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMalloc(&h->coef[c], cbytes);
-    if (e == cudaSuccess) e = cudaMalloc(&h->partial, sizeof(double) * 2 * size_t(h->nparts_max));
-    if (e == cudaSuccess) e = cudaMalloc(&h->pmax, sizeof(float) * size_t(h->nparts_max));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dstat, sizeof(DevStatus));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dflag, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&h->dclock, sizeof(unsigned));
+    auto galloc = [h](auto **p, size_t bytes) {
+        return glbm_guard::alloc(h->guards, reinterpret_cast<void **>(p), bytes, h->stream);
+    };
+    if (e == cudaSuccess) e = galloc(&h->buf[0], fbytes);
+    if (e == cudaSuccess) e = galloc(&h->buf[1], fbytes);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = galloc(&h->coef[c], cbytes);
+    if (e == cudaSuccess) e = galloc(&h->partial, sizeof(double) * 2 * size_t(h->nparts_max));
+    if (e == cudaSuccess) e = galloc(&h->pmax, sizeof(float) * size_t(h->nparts_max));
+    if (e == cudaSuccess) e = galloc(&h->dstat, sizeof(DevStatus));
+    if (e == cudaSuccess) e = galloc(&h->dflag, sizeof(int));
+    if (e == cudaSuccess) e = galloc(&h->dclock, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost(&h->hstat, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dstat, 0, sizeof(DevStatus), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dclock, 0, sizeof(unsigned), h->stream);
@@ -793,6 +801,13 @@ struct File {
 }  // namespace
 
 extern "C" {
+
+glbm_status glbm_debug_guards(glbm_t h, int poke, long long *damaged) {
+    if (glbm_status s = check(h)) return s;
+    if (!damaged) return fail(h, GLBM_EINVAL, "debug_guards: damaged is required");
+    CU(h, glbm_guard::count_damage(h->guards, h->stream, poke, damaged));
+    return GLBM_OK;
+}
 
 glbm_status glbm_save(glbm_t h, const char *path) {
     glbm_trace::Range trace_range("glbm_save");
