@@ -9,7 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", f) for f in ("glbm.cu", "batch.cu", "nn.cu", "nn_tc.cu", "nn_tc_train.cu", "em.cu")]
-HDR = [os.path.join(HERE, "csrc", n) for n in ("glbm_kernels.cuh", "setup_kernels.cuh", "tc_common.cuh", "trace.h")]
+HDR = [os.path.join(HERE, "csrc", n) for n in ("glbm_kernels.cuh", "setup_kernels.cuh", "tc_common.cuh", "trace.h", "guard.h")]
 OBJ = os.path.join(HERE, "csrc", "_obj")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libglbm.so")
