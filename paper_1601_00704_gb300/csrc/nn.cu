@@ -17,6 +17,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <cstdio>
 
 namespace {
@@ -147,55 +149,98 @@ k_conv_bwd_w(const float *__restrict__ x, long long xbs, int cin, const float *_
     }
 }
 
+// The element-wise kernels below run on a grid whose z index walks the
+// (sample, channel) planes, so that no thread divides a flat 64-bit index:
+// planes whose pixels are contiguous (ReLU mask, channel copies) are walked
+// in float4 runs where sizes and addresses allow; the resampling kernels
+// (pooling, upsampling) give each thread one pixel of a 32 x 8 tile.
+constexpr int kPlaneBlock = 256;
+
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// dy = 0 where y <= 0 (and where y is NaN), plane by plane
 __global__ void k_relu_bwd(const float *__restrict__ y, long long ybs, float *__restrict__ dy, long long dybs,
                            int c, long long hw, int n) {
-    const long long per = (long long)c * hw, total = per * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        if (!(y[s * ybs + r] > 0.0f)) dy[s * dybs + r] = 0.0f;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        const float *yp = y + s * ybs + ch * hw;
+        float *dp = dy + s * dybs + ch * hw;
+        const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+        if ((hw & 3) == 0 && aligned16(yp) && aligned16(dp)) {
+            const float4 *y4 = reinterpret_cast<const float4 *>(yp);
+            float4 *d4 = reinterpret_cast<float4 *>(dp);
+            for (long long i = t0; i < hw / 4; i += st) {
+                const float4 a = y4[i];
+                float4 g = d4[i];
+                g.x = a.x > 0.0f ? g.x : 0.0f;
+                g.y = a.y > 0.0f ? g.y : 0.0f;
+                g.z = a.z > 0.0f ? g.z : 0.0f;
+                g.w = a.w > 0.0f ? g.w : 0.0f;
+                d4[i] = g;
+            }
+        } else {
+            for (long long i = t0; i < hw; i += st)
+                if (!(yp[i] > 0.0f)) dp[i] = 0.0f;
+        }
     }
 }
 
-// dst[n][0:c] (=|+=) src[n][0:c]
+// dst[n][0:c] (=|+=) src[n][0:c], plane by plane
 __global__ void k_copy_ch(const float *__restrict__ src, long long sbs, float *__restrict__ dst, long long dbs, int c,
                           long long hw, int n, int accumulate) {
-    const long long per = (long long)c * hw, total = per * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        const float v = src[s * sbs + r];
-        if (accumulate) dst[s * dbs + r] += v;
-        else dst[s * dbs + r] = v;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        const float *sp = src + s * sbs + ch * hw;
+        float *dp = dst + s * dbs + ch * hw;
+        const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+        if ((hw & 3) == 0 && aligned16(sp) && aligned16(dp)) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(sp);
+            float4 *d4 = reinterpret_cast<float4 *>(dp);
+            for (long long i = t0; i < hw / 4; i += st) {
+                float4 v = s4[i];
+                if (accumulate) {
+                    const float4 o = d4[i];
+                    v.x += o.x;
+                    v.y += o.y;
+                    v.z += o.z;
+                    v.w += o.w;
+                }
+                d4[i] = v;
+            }
+        } else {
+            for (long long i = t0; i < hw; i += st) {
+                const float v = sp[i];
+                if (accumulate) dp[i] += v;
+                else dp[i] = v;
+            }
+        }
     }
 }
 
-// y (H/2 x W/2) = mean of 2x2 blocks of x (H x W)
+// y (H/2 x W/2) = mean of 2x2 blocks of x (H x W); one output pixel per thread
 __global__ void k_pool_fwd(const float *__restrict__ x, long long xbs, float *__restrict__ y, long long ybs, int c,
                            int H, int W, int n) {
     const int h2 = H / 2, w2 = W / 2;
-    const long long per = (long long)c * h2 * w2, total = per * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        const int ch = int(r / (h2 * w2)), p = int(r % (h2 * w2));
-        const int yy = p / w2, xx = p % w2;
-        const float *b = x + s * xbs + (long long)ch * H * W + (2 * yy) * W + 2 * xx;
-        y[s * ybs + r] = 0.25f * ((b[0] + b[1]) + (b[W] + b[W + 1]));
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (xx >= w2 || yy >= h2) return;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        const float *b = x + s * xbs + ch * H * W + (long long)(2 * yy) * W + 2 * xx;
+        y[s * ybs + ch * h2 * w2 + (long long)yy * w2 + xx] = 0.25f * ((b[0] + b[1]) + (b[W] + b[W + 1]));
     }
 }
 
+// dx (H x W) (=|+=) dy (H/2 x W/2) / 4 spread over each 2x2 block
 __global__ void k_pool_bwd(const float *__restrict__ dy, long long dybs, float *__restrict__ dx, long long dxbs, int c,
                            int H, int W, int n, int accumulate) {
-    const long long per = (long long)c * H * W, total = per * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        const int ch = int(r / ((long long)H * W)), p = int(r % ((long long)H * W));
-        const int yy = p / W, xx = p % W;
-        const float v = 0.25f * dy[s * dybs + (long long)ch * (H / 2) * (W / 2) + (yy / 2) * (W / 2) + xx / 2];
-        if (accumulate) dx[s * dxbs + r] += v;
-        else dx[s * dxbs + r] = v;
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (xx >= W || yy >= H) return;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        const float v = 0.25f * dy[s * dybs + ch * (H / 2) * (W / 2) + (long long)(yy / 2) * (W / 2) + xx / 2];
+        float *o = dx + s * dxbs + ch * H * W + (long long)yy * W + xx;
+        if (accumulate) *o += v;
+        else *o = v;
     }
 }
 
@@ -203,27 +248,24 @@ __global__ void k_pool_bwd(const float *__restrict__ dy, long long dybs, float *
 __global__ void k_up_fwd(const float *__restrict__ x, long long xbs, float *__restrict__ y, long long ybs, int c, int H,
                          int W, int n) {
     const int H2 = 2 * H, W2 = 2 * W;
-    const long long per = (long long)c * H2 * W2, total = per * n;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        const int ch = int(r / ((long long)H2 * W2)), p = int(r % ((long long)H2 * W2));
-        const int yy = p / W2, xx = p % W2;
-        y[s * ybs + r] = x[s * xbs + (long long)ch * H * W + (yy / 2) * W + xx / 2];
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (xx >= W2 || yy >= H2) return;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        y[s * ybs + ch * H2 * W2 + (long long)yy * W2 + xx] = x[s * xbs + ch * H * W + (long long)(yy / 2) * W + xx / 2];
     }
 }
 
+// dx (H x W) = sum over each 2x2 block of dy (2H x 2W)
 __global__ void k_up_bwd(const float *__restrict__ dy, long long dybs, float *__restrict__ dx, long long dxbs, int c,
                          int H, int W, int n) {
-    const long long per = (long long)c * H * W, total = per * n;
     const int W2 = 2 * W;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / per, r = i % per;
-        const int ch = int(r / ((long long)H * W)), p = int(r % ((long long)H * W));
-        const int yy = p / W, xx = p % W;
-        const float *b = dy + s * dybs + (long long)ch * 4 * H * W + (2 * yy) * W2 + 2 * xx;
-        dx[s * dxbs + r] = (b[0] + b[1]) + (b[W2] + b[W2 + 1]);
+    const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (xx >= W || yy >= H) return;
+    for (long long q = blockIdx.z; q < (long long)n * c; q += gridDim.z) {
+        const long long s = q / c, ch = q - s * c;
+        const float *b = dy + s * dybs + ch * 4 * H * W + (long long)(2 * yy) * W2 + 2 * xx;
+        dx[s * dxbs + ch * H * W + (long long)yy * W + xx] = (b[0] + b[1]) + (b[W2] + b[W2 + 1]);
     }
 }
 
@@ -262,6 +304,29 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     }
+}
+
+// Grids of the plane kernels: blocks of kPlaneBlock threads along each
+// (sample, channel) plane of `units` work items, planes along z.  About
+// kPlaneBlocks blocks in all: each block walks several planes, so that short
+// planes do not turn into one short-lived block per plane.
+constexpr long long kPlaneBlocks = 4096;
+unsigned plane_z(long long per_plane_blocks, long long planes) {
+    long long z = (kPlaneBlocks + per_plane_blocks - 1) / per_plane_blocks;
+    z = z < 1 ? 1 : z;
+    z = z > planes ? planes : z;
+    return unsigned(z > 65535 ? 65535 : z);
+}
+dim3 plane_grid(long long units, long long planes) {
+    long long gx = (units + kPlaneBlock - 1) / kPlaneBlock;
+    gx = gx < 1 ? 1 : (gx > 4096 ? 4096 : gx);
+    return dim3(unsigned(gx), 1, plane_z(gx, planes));
+}
+// ... and of the resampling kernels: 32 x 8 pixel tiles of the output plane.
+const dim3 kTile(32, 8);
+dim3 tile_grid(int w, int h, long long planes) {
+    const long long gx = (w + 31) / 32, gy = (h + 7) / 8;
+    return dim3(unsigned(gx), unsigned(gy), plane_z(gx * gy, planes));
 }
 
 int grid_for(long long total) {
@@ -324,7 +389,8 @@ glbm_status glbm_nn_relu_bwd(const float *y, long long ybs, float *dy, long long
                              void *stream) {
     if (!y || !dy || c < 1 || n < 1) return GLBM_EINVAL;
     const long long hw = (long long)h * w;
-    k_relu_bwd<<<grid_for(c * hw * n), 256, 0, static_cast<cudaStream_t>(stream)>>>(y, ybs, dy, dybs, c, hw, n);
+    k_relu_bwd<<<plane_grid((hw + 3) / 4, (long long)n * c), kPlaneBlock, 0, static_cast<cudaStream_t>(stream)>>>(
+        y, ybs, dy, dybs, c, hw, n);
     return launch_status();
 }
 
@@ -332,7 +398,7 @@ glbm_status glbm_nn_copy_channels(const float *src, long long sbs, float *dst, l
                                   int w, int accumulate, void *stream) {
     if (!src || !dst || c < 1 || n < 1) return GLBM_EINVAL;
     const long long hw = (long long)h * w;
-    k_copy_ch<<<grid_for(c * hw * n), 256, 0, static_cast<cudaStream_t>(stream)>>>(src, sbs, dst, dbs, c, hw, n,
+    k_copy_ch<<<plane_grid((hw + 3) / 4, (long long)n * c), kPlaneBlock, 0, static_cast<cudaStream_t>(stream)>>>(src, sbs, dst, dbs, c, hw, n,
                                                                                     accumulate);
     return launch_status();
 }
@@ -342,8 +408,9 @@ glbm_status glbm_nn_pool2(const float *x, long long xbs, float *y, long long ybs
     if (!x || !y || c < 1 || n < 1 || h % 2 || w % 2) return GLBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // forward: x (h x w) -> y (h/2 x w/2); backward: x = dy (h/2 x w/2) -> y = dx (h x w)
-    if (!backward) k_pool_fwd<<<grid_for((long long)c * h * w / 4 * n), 256, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
-    else k_pool_bwd<<<grid_for((long long)c * h * w * n), 256, 0, st>>>(x, xbs, y, ybs, c, h, w, n, accumulate);
+    const long long planes = (long long)n * c;
+    if (!backward) k_pool_fwd<<<tile_grid(w / 2, h / 2, planes), kTile, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
+    else k_pool_bwd<<<tile_grid(w, h, planes), kTile, 0, st>>>(x, xbs, y, ybs, c, h, w, n, accumulate);
     return launch_status();
 }
 
@@ -352,8 +419,9 @@ glbm_status glbm_nn_upsample2(const float *x, long long xbs, float *y, long long
     if (!x || !y || c < 1 || n < 1) return GLBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // forward: x (h x w) -> y (2h x 2w); backward: x = dy (2h x 2w) -> y = dx (h x w)
-    if (!backward) k_up_fwd<<<grid_for((long long)c * h * w * 4 * n), 256, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
-    else k_up_bwd<<<grid_for((long long)c * h * w * n), 256, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
+    const long long planes = (long long)n * c;
+    if (!backward) k_up_fwd<<<tile_grid(2 * w, 2 * h, planes), kTile, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
+    else k_up_bwd<<<tile_grid(w, h, planes), kTile, 0, st>>>(x, xbs, y, ybs, c, h, w, n);
     return launch_status();
 }
 

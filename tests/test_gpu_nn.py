@@ -113,3 +113,86 @@ def test_pool_upsample_copy_ops(env):
     torch.cuda.synchronize()
     assert np.array_equal(big.cpu().numpy()[:, 2:], x)
     assert not big.cpu().numpy()[:, :2].any()
+
+
+@pytest.mark.parametrize("h,w", [(8, 12), (7, 9), (20, 70)], ids=["aligned", "ragged", "tiles"])
+def test_elementwise_kernels_on_channel_slices(env, h, w):
+    """ReLU mask, channel copy, 2x2 pooling and nearest upsampling, forward
+    and backward, on a 3-channel slice (channels 1-3) of 5-channel tensors,
+    against NumPy in the kernels' FP32 operation order: bit for bit.  hw a
+    multiple of 4 with 16-byte aligned planes takes the float4 path, the
+    others the scalar one; (20, 70) spans several 32 x 8 pixel tiles."""
+    pkg, _, torch = env
+    lib = pkg.load()
+    rng = np.random.default_rng(h * 100 + w)
+    n, c, C5 = 2, 3, 5
+    f32 = np.float32
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=f32)).cuda()
+
+    def sl(t, hh, ww):  # pointer to channel 1 of a (n, 5, hh, ww) tensor, sample stride
+        return t.data_ptr() + 4 * hh * ww, C5 * hh * ww
+
+    # ReLU backward: dy = 0 where y <= 0 (also NaN)
+    y = rng.normal(size=(n, C5, h, w)).astype(f32)
+    y[0, 1, 0, 0] = np.nan
+    dy = rng.normal(size=(n, C5, h, w)).astype(f32)
+    ty, tdy = dev(y), dev(dy)
+    assert lib.glbm_nn_relu_bwd(*sl(ty, h, w), *sl(tdy, h, w), c, n, h, w, None) == 0
+    want = dy.copy()
+    want[:, 1:4] = np.where(y[:, 1:4] > 0, dy[:, 1:4], f32(0))
+    torch.cuda.synchronize()
+    assert np.array_equal(tdy.cpu().numpy(), want)
+
+    # channel copy, plain and accumulating
+    src = rng.normal(size=(n, C5, h, w)).astype(f32)
+    dst = rng.normal(size=(n, C5, h, w)).astype(f32)
+    ts, td = dev(src), dev(dst)
+    assert lib.glbm_nn_copy_channels(*sl(ts, h, w), *sl(td, h, w), c, n, h, w, 1, None) == 0
+    want = dst.copy()
+    want[:, 1:4] = dst[:, 1:4] + src[:, 1:4]
+    torch.cuda.synchronize()
+    assert np.array_equal(td.cpu().numpy(), want)
+    assert lib.glbm_nn_copy_channels(*sl(ts, h, w), *sl(td, h, w), c, n, h, w, 0, None) == 0
+    want[:, 1:4] = src[:, 1:4]
+    torch.cuda.synchronize()
+    assert np.array_equal(td.cpu().numpy(), want)
+
+    # nearest upsampling h x w -> 2h x 2w and its adjoint
+    x = rng.normal(size=(n, C5, h, w)).astype(f32)
+    up = rng.normal(size=(n, C5, 2 * h, 2 * w)).astype(f32)
+    tx, tu = dev(x), dev(up)
+    assert lib.glbm_nn_upsample2(*sl(tx, h, w), *sl(tu, 2 * h, 2 * w), c, n, h, w, 0, None) == 0
+    want = up.copy()
+    want[:, 1:4] = x[:, 1:4].repeat(2, axis=2).repeat(2, axis=3)
+    torch.cuda.synchronize()
+    assert np.array_equal(tu.cpu().numpy(), want)
+    g = rng.normal(size=(n, C5, 2 * h, 2 * w)).astype(f32)
+    dx = rng.normal(size=(n, C5, h, w)).astype(f32)
+    tg, tdx = dev(g), dev(dx)
+    assert lib.glbm_nn_upsample2(*sl(tg, 2 * h, 2 * w), *sl(tdx, h, w), c, n, h, w, 1, None) == 0
+    want = dx.copy()
+    gs = g[:, 1:4]
+    want[:, 1:4] = (gs[..., 0::2, 0::2] + gs[..., 0::2, 1::2]) + (gs[..., 1::2, 0::2] + gs[..., 1::2, 1::2])
+    torch.cuda.synchronize()
+    assert np.array_equal(tdx.cpu().numpy(), want)
+
+    # 2x2 average pooling 2h x 2w -> h x w and its adjoint (accumulating)
+    big = rng.normal(size=(n, C5, 2 * h, 2 * w)).astype(f32)
+    small = rng.normal(size=(n, C5, h, w)).astype(f32)
+    tb, tsm = dev(big), dev(small)
+    assert lib.glbm_nn_pool2(*sl(tb, 2 * h, 2 * w), *sl(tsm, h, w), c, n, 2 * h, 2 * w, 0, 0, None) == 0
+    want = small.copy()
+    bs = big[:, 1:4]
+    want[:, 1:4] = f32(0.25) * ((bs[..., 0::2, 0::2] + bs[..., 0::2, 1::2]) + (bs[..., 1::2, 0::2] + bs[..., 1::2, 1::2]))
+    torch.cuda.synchronize()
+    assert np.array_equal(tsm.cpu().numpy(), want)
+    pooled = want  # now the pooling backward's input (dy)
+    acc = rng.normal(size=(n, C5, 2 * h, 2 * w)).astype(f32)
+    ta = dev(acc)
+    assert lib.glbm_nn_pool2(*sl(tsm, h, w), *sl(ta, 2 * h, 2 * w), c, n, 2 * h, 2 * w, 1, 1, None) == 0
+    want = acc.copy()
+    want[:, 1:4] = acc[:, 1:4] + (f32(0.25) * pooled[:, 1:4]).repeat(2, axis=2).repeat(2, axis=3)
+    torch.cuda.synchronize()
+    assert np.array_equal(ta.cpu().numpy(), want)
