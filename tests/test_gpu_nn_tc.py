@@ -282,6 +282,26 @@ def test_tc_conv_rejects_bad_shapes(pkg):
     assert b"k = 1 or 3" in lib.glbm_last_error(None)
 
 
+@pytest.mark.parametrize("n,c,h,w,cp", [(1, 90, 9, 37, 96), (2, 3, 4, 4, 264), (3, 128, 8, 8, 128),
+                                         (1, 32, 64, 64, 32)],
+                         ids=["ragged-run", "two-slices", "small", "aligned"])
+def test_nchw_to_nhwc_matches_torch(pkg, n, c, h, w, cp):
+    """FP32 NCHW -> BF16 NHWC (zero-padded to cp channels) bit for bit against
+    torch's round-to-nearest-even conversion: a run of pixels shorter than 32
+    at the end of each image, more than 256 channels (two slices of the
+    shared-memory tile), small and aligned tensors."""
+    import torch
+    lib = pkg.load()
+    rng = np.random.default_rng(c * 1000 + h * w)
+    x = rng.normal(size=(n, c, h, w)).astype(np.float32)
+    y = torch.full((n, h, w, cp), 7.0, dtype=torch.bfloat16, device="cuda")
+    assert lib.glbm_nn_nchw_to_nhwc(_vp(torch.from_numpy(x).cuda()), n, c, h, w, _vp(y), cp, _stream()) == 0
+    expect = np.zeros((n, h, w, cp), dtype=np.float32)
+    expect[..., :c] = x.transpose(0, 2, 3, 1)
+    torch.cuda.synchronize()
+    assert torch.equal(y.cpu(), torch.from_numpy(expect).to(torch.bfloat16))
+
+
 def test_nhwc_layout_kernels(pkg):
     import torch
     lib = pkg.load()
