@@ -168,6 +168,32 @@ def test_two_phase_medium_momentum_balance(orc, G, F_eps):
         assert np.sum(o.rho * eps * F_eps / np.sqrt(K) * speed * o.ux) > 1e3 * bound
 
 
+@pytest.mark.parametrize("F_eps", [0.0, 2.0], ids=["darcy", "forchheimer"])
+def test_force_reversal_is_the_mirror_image(orc, F_eps):
+    """A two-phase medium symmetric under x -> nx-1-x (periodic x, walls in
+    y): reversing G is the same problem mirrored, so after any number of
+    steps u_x(-G) = -u_x(G) and u_y, rho agree at mirrored columns, up to
+    the order of FP64 sums.  D2Q9 streaming, Guo forcing (Eqs. 29-31) and
+    the velocity of Eqs. 33-35 each commute with the reflection; a wrong
+    lattice vector, streaming direction or force sign breaks it."""
+    eps0, K0, _ = media.two_phase_medium(24, 16, seed=5)
+    eps = np.maximum(eps0, eps0[:, ::-1])  # mirror-symmetric in x
+    K = np.maximum(K0, K0[:, ::-1])
+    G = 1e-4
+    runs = []
+    for g in (G, -G):
+        o = run(orc, eps, K, (g, 3e-5), tau=0.8, steps=700, tol=0.0, feps=F_eps)
+        runs.append(o)
+    a, b = runs
+    # u is resolved from sums of f ~ w_i ~ 0.1, i.e. to ~1e-17 per sum in
+    # FP64, and the two runs add the mirrored populations in other orders;
+    # a broken symmetry shows at the size of u itself (here ~1e-6)
+    assert np.abs(a.ux).max() > 1e-7
+    np.testing.assert_allclose(b.ux, -a.ux[:, ::-1], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(b.uy, a.uy[:, ::-1], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(b.rho, a.rho[:, ::-1], rtol=0, atol=1e-13)
+
+
 def test_parallel_layers_arithmetic_mean(orc):
     """Layers parallel to the flow, periodic y (the 'parallel' arrangement):
     away from Brinkman layers of width sqrt(K/eps) each layer carries its
