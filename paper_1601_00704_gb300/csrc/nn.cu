@@ -387,7 +387,7 @@ glbm_status glbm_nn_conv_bwd_weight(const float *x, long long xbs, int cin, cons
 
 glbm_status glbm_nn_relu_bwd(const float *y, long long ybs, float *dy, long long dybs, int c, int n, int h, int w,
                              void *stream) {
-    if (!y || !dy || c < 1 || n < 1) return GLBM_EINVAL;
+    if (!y || !dy || c < 1 || n < 1 || h < 1 || w < 1) return GLBM_EINVAL;
     const long long hw = (long long)h * w;
     k_relu_bwd<<<plane_grid((hw + 3) / 4, (long long)n * c), kPlaneBlock, 0, static_cast<cudaStream_t>(stream)>>>(
         y, ybs, dy, dybs, c, hw, n);
@@ -396,7 +396,7 @@ glbm_status glbm_nn_relu_bwd(const float *y, long long ybs, float *dy, long long
 
 glbm_status glbm_nn_copy_channels(const float *src, long long sbs, float *dst, long long dbs, int c, int n, int h,
                                   int w, int accumulate, void *stream) {
-    if (!src || !dst || c < 1 || n < 1) return GLBM_EINVAL;
+    if (!src || !dst || c < 1 || n < 1 || h < 1 || w < 1) return GLBM_EINVAL;
     const long long hw = (long long)h * w;
     k_copy_ch<<<plane_grid((hw + 3) / 4, (long long)n * c), kPlaneBlock, 0, static_cast<cudaStream_t>(stream)>>>(src, sbs, dst, dbs, c, hw, n,
                                                                                     accumulate);
@@ -405,7 +405,7 @@ glbm_status glbm_nn_copy_channels(const float *src, long long sbs, float *dst, l
 
 glbm_status glbm_nn_pool2(const float *x, long long xbs, float *y, long long ybs, int c, int n, int h, int w,
                           int backward, int accumulate, void *stream) {
-    if (!x || !y || c < 1 || n < 1 || h % 2 || w % 2) return GLBM_EINVAL;
+    if (!x || !y || c < 1 || n < 1 || h < 2 || w < 2 || h % 2 || w % 2) return GLBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // forward: x (h x w) -> y (h/2 x w/2); backward: x = dy (h/2 x w/2) -> y = dx (h x w)
     const long long planes = (long long)n * c;
@@ -416,7 +416,7 @@ glbm_status glbm_nn_pool2(const float *x, long long xbs, float *y, long long ybs
 
 glbm_status glbm_nn_upsample2(const float *x, long long xbs, float *y, long long ybs, int c, int n, int h, int w,
                               int backward, void *stream) {
-    if (!x || !y || c < 1 || n < 1) return GLBM_EINVAL;
+    if (!x || !y || c < 1 || n < 1 || h < 1 || w < 1) return GLBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // forward: x (h x w) -> y (2h x 2w); backward: x = dy (2h x 2w) -> y = dx (h x w)
     const long long planes = (long long)n * c;

@@ -48,6 +48,19 @@ def test_create_error_message_without_device(lib):
     lib.glbm_destroy(None)  # NULL-safe
 
 
+def test_elementwise_entry_points_reject_empty_images(lib):
+    """Sizes are checked on the host before any CUDA call (so this runs
+    without a GPU; the placeholder pointers are never dereferenced):
+    images without pixels, and odd sizes for 2x2 pooling, are EINVAL."""
+    import ctypes as C
+    p = C.c_void_p(256)
+    assert lib.glbm_nn_relu_bwd(p, 0, p, 0, 3, 2, 0, 8, None) == -1
+    assert lib.glbm_nn_copy_channels(p, 0, p, 0, 3, 2, 8, 0, 0, None) == -1
+    for h, w in ((0, 8), (8, 0), (1, 8), (7, 8)):
+        assert lib.glbm_nn_pool2(p, 0, p, 0, 3, 2, h, w, 0, 0, None) == -1
+    assert lib.glbm_nn_upsample2(p, 0, p, 0, 3, 2, 0, 4, 0, None) == -1
+
+
 def test_no_oracle_in_product():
     """The product package never imports the oracle (it is test-only)."""
     pkgdir = os.path.join(ROOT, "paper_1601_00704_gb300")
