@@ -61,6 +61,26 @@ def test_elementwise_entry_points_reject_empty_images(lib):
     assert lib.glbm_nn_upsample2(p, 0, p, 0, 3, 2, 0, 4, 0, None) == -1
 
 
+def test_tensor_core_entry_points_validate_on_the_host(lib):
+    """The weight gradient and the layout conversion reject bad sizes and
+    misaligned pointers with EINVAL and a message before any CUDA call."""
+    import ctypes as C
+    p, q = C.c_void_p(256), C.c_void_p(256 + 4)
+
+    def wgrad(x=p, cx=32, cin=32, cy=32, cout=32, k=3):
+        return lib.glbm_nn_tc_conv_wgrad(x, cx, cin, p, cy, cout, 2, 8, 8, k, p, p, None)
+
+    assert wgrad(k=5) == -1 and b"k = 1 or 3" in lib.glbm_last_error(None)
+    assert wgrad(cx=48) == -1 and b"multiples of 32" in lib.glbm_last_error(None)
+    assert wgrad(cy=288, cout=288) == -1
+    assert wgrad(cin=40) == -1      # more real input channels than the tensor holds
+    assert wgrad(x=q) == -1 and b"16-byte aligned" in lib.glbm_last_error(None)
+    assert lib.glbm_nn_nchw_to_nhwc(p, 2, 5, 4, 4, p, 12, None) == -1     # c_pad not a multiple of 8
+    assert lib.glbm_nn_nchw_to_nhwc(p, 2, 20, 4, 4, p, 16, None) == -1    # c_pad < c
+    assert lib.glbm_nn_nchw_to_nhwc(p, 2, 5, 4, 4, q, 16, None) == -1     # y not 16-byte aligned
+    assert b"16-byte aligned" in lib.glbm_last_error(None)
+
+
 def test_no_oracle_in_product():
     """The product package never imports the oracle (it is test-only)."""
     pkgdir = os.path.join(ROOT, "paper_1601_00704_gb300")
